@@ -1,0 +1,128 @@
+"""Pins of oracle populations and line terms (not gpu)."""
+import json
+import math
+import os
+
+import numpy as np
+from scipy import integrate
+
+import workloads as wl
+from oracle import physics as ph
+from oracle.voigt import H
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "textbook_values.json")))
+
+
+def hydrogen_only():
+    return wl.Elements(["H"], np.array([1.008]), np.array([13.598]), np.array([2.0]), np.array([1.0]), np.array([12.0]))
+
+
+def test_pure_hydrogen_closed_form():
+    # x = n_e/n_nuc; P = (1 + x) n_nuc kT and x^2/(1-x) = Phi/n_nuc give x = sqrt(Phi kT/(P + Phi kT))
+    el = hydrogen_only()
+    k = 1.380649e-16
+    for T in [3000.0, 6000.0, 9000.0, 15000.0, 50000.0]:
+        for P in [1e-2, 1e2, 1e4, 1e7]:
+            phi = 2 * 1.0 / 2.0 * (2 * math.pi * 9.1093837015e-28 * k * T / 6.62607015e-27 ** 2) ** 1.5 \
+                * math.exp(-13.598 * 1.602176634e-12 / (k * T))
+            x = math.sqrt(phi * k * T / (P + phi * k * T))
+            pop = ph.populations(T, P, el)
+            assert abs(pop.n_e / pop.n_nuc / x - 1) < 1e-11, (T, P)
+
+
+def test_conservation():
+    el = wl.elements(15)
+    rng = np.random.default_rng(1)
+    for T, P in zip(np.exp(rng.uniform(math.log(2000), math.log(2e5), 20)), 10 ** rng.uniform(-4, 8, 20)):
+        pop = ph.populations(T, P, el, abund_scale=np.exp(rng.uniform(-4, 2, el.n)))
+        assert abs(pop.n_stage[:, 1].sum() / pop.n_e - 1) < 1e-12          # charge
+        assert abs((pop.n_nuc + pop.n_e) * ph.K_BOLTZ * T / P - 1) < 1e-12  # particles
+        assert np.all(pop.n_stage >= 0)
+
+
+def one_line(lam_nm, loggf, E, sp, lgR=-8.0, lgS=-8.0, lgW=-8.0):
+    f32 = lambda x: np.array([x], dtype=np.float32)
+    return wl.LineList(np.array([lam_nm]), f32(loggf), f32(E), np.array([sp], dtype=np.int32), f32(lgR), f32(lgS), f32(lgW))
+
+
+def test_integrated_cross_section():
+    # integral over nu of ell equals (pi e^2/(m_e c)) g f (N/U)/rho e^{-E/kT}(1-e^{-h nu/kT}); with E = 0 and
+    # h nu/kT = 36 the last two factors are 1, so rho * int ell dnu / (g f N/U) must equal 0.02654 cm^2 Hz
+    el = wl.elements(5); se, ss = wl.species_table(5)
+    pop = ph.populations(4000.0, 1e4, el)
+    L = one_line(100.0, 0.0, 0.0, 0)
+    t = ph.line_terms(L, se, ss, el, pop)
+    S, a, dnu = t.S[0], t.a[0], t.dnuD[0]
+    val, _ = integrate.quad(lambda v: H(v, a), 0, np.inf, limit=400, epsabs=0, epsrel=1e-10)
+    integral = 2 * val * S * dnu            # int ell dnu = S dnuD int H dv
+    sigma = integral * pop.rho / pop.NU[se[0], ss[0]]
+    g = GOLD["classical_oscillator_cross_section_cm2_Hz"]
+    assert abs(sigma / g["value"] - 1) < g["rtol"]
+
+
+def test_boltzmann_factor():
+    el = wl.elements(5); se, ss = wl.species_table(5)
+    pop = ph.populations(6000.0, 1e4, el)
+    t1 = ph.line_terms(one_line(350.0, -2.0, 1.0, 2), se, ss, el, pop)
+    t2 = ph.line_terms(one_line(350.0, -2.0, 3.5, 2), se, ss, el, pop)
+    kB = GOLD["boltzmann_eV_per_K"]["value"]
+    assert abs(t2.S[0] / t1.S[0] / math.exp(-2.5 / (kB * 6000.0)) - 1) < 1e-6
+
+
+def test_doppler_width_hydrogen():
+    # a line of a hydrogen-mass species: dnuD/nu0 = sqrt(2kT/m_H)/c
+    el = wl.Elements(["H", "He", "X"], np.array([1.008, 4.0026, 1.008]), np.array([13.598, 24.587, 13.598]),
+                     np.array([2.0, 1.0, 2.0]), np.array([1.0, 2.0, 1.0]), np.array([12.0, 10.93, 6.0]))
+    se, ss = np.array([2, 2], dtype=np.int32), np.array([0, 1], dtype=np.int32)
+    pop = ph.populations(1e4, 1e4, el)
+    t = ph.line_terms(one_line(500.0, 0.0, 0.0, 0), se, ss, el, pop)
+    vth = t.dnuD[0] / t.nu0[0] * 2.99792458e10 / 1e5
+    g = GOLD["hydrogen_thermal_speed_1e4K_km_s"]
+    assert abs(vth / g["value"] - 1) < g["rtol"]
+    # thermal width scales as sqrt(T)
+    pop4 = ph.populations(4e4, 1e4, el)
+    t4 = ph.line_terms(one_line(500.0, 0.0, 0.0, 0), se, ss, el, pop4)
+    assert abs(t4.dnuD[0] / t.dnuD[0] - 2.0) < 1e-12
+
+
+def test_lorentz_width():
+    # for a >> 1 the profile is Lorentzian with FWHM in frequency gamma/(2 pi): ell(dnu = gamma/(4 pi)) = ell(0)/2
+    el = wl.elements(5); se, ss = wl.species_table(5)
+    pop = ph.populations(6000.0, 1e8, el)
+    L = one_line(350.0, -2.0, 1.0, 0, lgR=15.0, lgS=-30.0, lgW=-30.0)
+    t = ph.line_terms(L, se, ss, el, pop)
+    a = t.a[0]
+    assert a > 100
+    v_half = t.gamma[0] / (4 * math.pi) / t.dnuD[0]
+    assert abs(H(v_half, a) / H(0.0, a) - 0.5) < 2 / a ** 2
+
+
+def test_density_pure_hydrogen():
+    # rho = n_nuc * m_H with the textbook hydrogen-atom mass 1.6735575e-24 g (the table carries the rounded weight 1.008 amu: 1.6e-4)
+    pop = ph.populations(8000.0, 1e4, hydrogen_only())
+    assert abs(pop.rho / (pop.n_nuc * 1.6735575e-24) - 1) < 3e-4
+    # stage I of hydrogen has U = 2: N/U = n_HI / 2
+    assert abs(pop.NU[0, 0] / (pop.n_HI / 2.0) - 1) < 1e-15
+
+
+def test_stimulated_emission_and_lambda_scaling():
+    # at h nu/kT = ln 2 the stimulated-emission factor is 1/2; S also scales as 1/dnuD, i.e. as lambda
+    el = wl.elements(5); se, ss = wl.species_table(5)
+    T = 6000.0
+    pop = ph.populations(T, 1e4, el)
+    lam_half = 6.62607015e-27 * 2.99792458e10 / (1.380649e-16 * T * math.log(2.0)) * 1e7  # nm
+    lam_one = 50.0  # h nu/kT = 48
+    s_half = ph.line_terms(one_line(lam_half, -1.0, 2.0, 4), se, ss, el, pop).S[0]
+    s_one = ph.line_terms(one_line(lam_one, -1.0, 2.0, 4), se, ss, el, pop).S[0]
+    assert abs(s_half / s_one / (0.5 * lam_half / lam_one) - 1) < 1e-12
+
+
+def test_pressure_broadening_perturbers():
+    # Stark width scales with n_e and van der Waals width with n_HI: FWHM = 10^lg * n / (2 pi)
+    el = wl.elements(5); se, ss = wl.species_table(5)
+    pop = ph.populations(9000.0, 1e8, el)
+    tS = ph.line_terms(one_line(350.0, -2.0, 1.0, 0, lgR=-30.0, lgS=-2.0, lgW=-30.0), se, ss, el, pop)
+    tW = ph.line_terms(one_line(350.0, -2.0, 1.0, 0, lgR=-30.0, lgS=-30.0, lgW=-2.0), se, ss, el, pop)
+    assert abs(tS.gamma[0] / (1e-2 * pop.n_e) - 1) < 1e-6
+    assert abs(tW.gamma[0] / (1e-2 * pop.n_HI) - 1) < 1e-6
+    assert abs(tS.a[0] * 4 * math.pi * tS.dnuD[0] / tS.gamma[0] - 1) < 1e-14
