@@ -80,8 +80,10 @@ def populations(T: float, P: float, el, abund_scale=None) -> Populations:
             break
     n_e = math.exp(0.5 * (lo + hi))
     n_nuc = n_tot - n_e
+    # n_II/n_I = Phi/n_e: n_I = f n_nuc n_e/(n_e + Phi) avoids the cancellation of f n_nuc - n_II
+    # when stage I is almost fully ionised
     n2 = frac * n_nuc * phi / (n_e + phi)
-    n1 = frac * n_nuc - n2
+    n1 = frac * n_nuc * n_e / (n_e + phi)
     rho = n_nuc * float(np.sum(frac * el.mass_amu * AMU))
     stage = np.stack([n1, n2], axis=1)
     NU = np.stack([n1 / el.U1, n2 / el.U2], axis=1)
