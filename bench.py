@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the line-opacity + ODF hot path on the full ODF-table workload.
+
+Workload: 5e6 seeded synthetic lines (30 species) over 9-10000 nm on an R = 2e6
+log-lambda grid (14,026,236 points), the 57 x 25 DFSYNTHE T-P grid, 328 equal
+log-lambda intervals x 12 ODF steps.  One step = one batch of (T, P) points of
+that table through the whole hot path: populations are resident, then
+synth_opacity (line prep, cut, profile synthesis) and build_odf (sort + step
+means).  Metric: Voigt line-evaluations per second (the number of (line, grid
+point) profile evaluations inside the cut windows, counted by the library),
+plus ODF (T, P) points per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+Under torchrun each rank takes its own batch of points (independent units, no
+data-path collective; weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "Voigt line-evals/s (line-by-line opacity synthesis + ODF binning)"
+UNIT = "line-evals/s"
+# FP32 operations of one far-wing profile evaluation (the tier that takes > 98% of
+# evaluations): v = fma(G, kvB, kvE1); V-term fma; reciprocal argument; y(2+4y) fma;
+# two multiplies by strength; accumulate: 3 FFMA (6 flop) + 3 FMUL + 1 FADD = 10 flop.
+FLOP_PER_EVAL = 10
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def batch_points(rank: int, B: int):
+    """A fixed stratified batch of the 57 x 25 table for each rank: T and P indices
+    spread over the whole grid (Latin-hypercube style), shifted per rank."""
+    rng = np.random.default_rng(4242 + rank)
+    ti = (np.linspace(2, 54, B).round().astype(int) + rank * 3) % 57
+    pi = rng.permutation(np.linspace(1, 23, B).round().astype(int))
+    return (ti * 25 + pi).astype(np.int32)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    except (OSError, ValueError):
+        return 6800.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+def oracle_sample(seconds: float, w, lines, row_T, row_P):
+    """Time the FP64 oracle (as it stands) on contiguous 0.2 nm slices of the same line list:
+    each slice's lines, synthesised densely on the slice's grid at one (T, P) point, then the
+    slice's ODF.  Returns (evals/s, evals, wall s, description)."""
+    from oracle import odf as od
+    from oracle import synthesis as sy
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    rng = np.random.default_rng(99)
+    evals, t_total, n_slices = 0, 0.0, 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < seconds:
+        lam0 = float(np.exp(rng.uniform(math.log(200.0), math.log(2000.0))))
+        lam1 = lam0 + 0.2
+        i0, i1 = np.searchsorted(lines.lam_nm, [lam0, lam1])
+        if i1 - i0 < 2:
+            continue
+        sub = lines.subset(slice(i0, i1))
+        g = wl.Grid(lam0, lam1, w.grid.R)
+        t0 = time.perf_counter()
+        pl = sy.prepare(sub, se, ss, el, row_T, row_P, g, w.cut, w.kc_factor)
+        k, _, W = sy.kappa_dense(pl)
+        od.odf(k, wl.equal_intervals(pl.N, 2), w.widths)
+        t_total += time.perf_counter() - t0
+        evals += W
+        n_slices += 1
+    desc = (f"{n_slices} slices of 0.2 nm (lines of the 5e6-line list inside each slice, dense FP64 synthesis "
+            f"on the slice grid at R=2e6 and T={row_T:.0f} K, P={row_P:.3g}, plus the slice ODF)")
+    return evals / t_total, evals, t_total, desc
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = wl.config_table()
+    lines = w.lines()
+    pts = batch_points(0, args.batch)
+    T, P = w.T[pts[0]], w.P[pts[0]]
+    per_step = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(per_step / 4, w, lines, T, P)
+    vals, evs, secs = [], 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, e, s, desc = oracle_sample(per_step, w, lines, T, P)
+        vals.append(v)
+        evs += e
+        secs += s
+    value = evs / secs
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "sample": "bounded oracle sample per step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def native_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2105_13611_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    ctx = binding.Context(local)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    K = w.n_intervals
+    bounds = wl.equal_intervals(N, K)
+    sel = batch_points(rank, args.batch)
+    B = len(sel)
+    stream = torch.cuda.current_stream()
+    kap = torch.empty((B, N), dtype=torch.float32, device=dev)
+    kc = torch.empty(B, dtype=torch.float32, device=dev)
+    ev = torch.empty(B, dtype=torch.int64, device=dev)
+    ev_tot = torch.zeros(B, dtype=torch.int64, device=dev)
+    odf = torch.empty((B, K, 12), dtype=torch.float64, device=dev)
+    opts = binding.make_opts(w.cut, w.kc_factor)
+
+    def step():
+        ctx.synth_opacity(w.grid, sel, kap, kc, ev, opts=opts, stream=stream)
+        ctx.build_odf(kap, bounds, w.widths, odf, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    ctx.profile_enable(True)
+    ctx.profile_read(binding.KERNEL_PROFILE)
+    ctx.profile_read(binding.KERNEL_ODF)
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        ev_tot.add_(ev)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    tiles_ms, tiles_n = ctx.profile_read(binding.KERNEL_PROFILE)
+    odf_ms, odf_n = ctx.profile_read(binding.KERNEL_ODF)
+    ctx.profile_enable(False)
+    evals_rank = float(ev_tot.sum().item())
+    evals = sum_over_ranks(evals_rank)
+    ms_max = max_over_ranks(ms)
+    value = evals / (ms_max / 1e3)
+    odf_pts = B * args.steps * world / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Tb = np.ascontiguousarray(w.T[sel])
+        Pb = np.ascontiguousarray(w.P[sel])
+        odf_h = torch.empty((B, K, 12), dtype=torch.float64, pin_memory=True)
+        kc_h = torch.empty(B, dtype=torch.float32, pin_memory=True)
+        ev_h = torch.empty(B, dtype=torch.int64, pin_memory=True)
+        rows = np.arange(B, dtype=np.int32)
+        ctx2 = binding.Context(local)
+        ctx2.load_linelist(lines, se, ss)
+
+        def e2e_step():
+            ctx2.set_atmosphere_grid(el, Tb, Pb)
+            ctx2.synth_opacity(w.grid, rows, kap, kc, ev, opts=opts, stream=stream)
+            ctx2.build_odf(kap, bounds, w.widths, odf, stream=stream)
+            odf_h.copy_(odf, non_blocking=True)
+            kc_h.copy_(kc, non_blocking=True)
+            ev_h.copy_(ev, non_blocking=True)
+            stream.synchronize()
+            return int(ev_h.sum())
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        ev_e2e = 0
+        for _ in range(args.steps):
+            ev_e2e += e2e_step()
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        ev_e2e = sum_over_ranks(ev_e2e)
+        n_el = el.n
+        h2d = (Tb.nbytes + Pb.nbytes + 5 * n_el * 8 + n_el * 8          # set_atmosphere_grid
+               + rows.nbytes                                           # synth_opacity rows
+               + bounds.nbytes + 8 * (2 * len(w.widths) + 1))          # build_odf bounds and widths
+        d2h = odf_h.numel() * 8 + kc_h.numel() * 4 + ev_h.numel() * 8
+        e2e = {"value": ev_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "note": "line list resident (loaded once); per step: populations from host T, P, synthesis, ODF, "
+                       "ODF table + kappa_c + evaluation counts copied to pinned host memory"}
+        ctx2.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, sm_max, peak_kind = peaks()
+    tiles_avg = tiles_ms / max(tiles_n, 1)
+    evals_per_launch = evals_rank / max(tiles_n, 1)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
+    achieved = evals_per_launch * FLOP_PER_EVAL / (tiles_avg / 1e3) / 1e12
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_path):
+        try:
+            traffic = json.load(open(prof_path)).get("k_tiles_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_tiles (profile synthesis)",
+                "peak_kind": f"FP32 FMA peak {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
+                "flop_per_eval": FLOP_PER_EVAL, "avg_launch_ms": tiles_avg, "launches": tiles_n}
+    odf_avg = odf_ms / max(odf_n, 1)
+    odf_bytes = B * N * 4 + B * K * 12 * 8
+    roofline_odf = {"bound": "hbm", "achieved": odf_bytes / (odf_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": odf_bytes / (odf_avg / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_odf (build_odf)",
+                    "peak_kind": f"{peak_kind} HBM copy bandwidth", "avg_launch_ms": odf_avg, "launches": odf_n}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, e, s, desc = oracle_sample(15.0, w, lines, float(w.T[sel[0]]), float(w.P[sel[0]]))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "evals": int(e), "seconds": s}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "lines": len(lines), "species": w.n_species, "grid_points": N,
+                      "R": w.grid.R, "lambda_nm": [w.grid.lam0_nm, w.grid.lam1_nm], "tp_grid": "57 T x 25 P",
+                      "points_per_step_per_rank": B, "rows": [int(x) for x in sel], "intervals": K, "odf_steps": 12,
+                      "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"independent points x{world}"},
+           "odf_points_per_s": odf_pts, "evals_per_step": evals / args.steps,
+           "roofline": roofline, "roofline_odf": roofline_odf, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": 10 * args.steps, "clocks": clk}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        native_arm(args)
+
+
+if __name__ == "__main__":
+    main()

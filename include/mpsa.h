@@ -1,0 +1,229 @@
+/*
+ * mpsa.h -- C ABI of the GB300 line-opacity / ODF / spectrum library.
+ *
+ * The library implements the data-parallel hot path of the MPS-ATLAS opacity
+ * module (Witzke et al. 2021, arXiv 2105.13611): line-by-line opacity synthesis
+ * (Sect. 2.1, Eq. l_nu_line; App. E), ODF binning (Sect. 2.3; App. E) and an LTE
+ * emergent-intensity formal solution (Sect. 2.2, Eq. Ilambda).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: MPSA_OK (0) or a negative MPSA_E* code.  mpsa_last_error()
+ *    returns a human-readable message for the calling thread's last failure.
+ *  - Units are cgs; wavelengths at the API are in nm, energies in eV.
+ *  - "host" pointers are read during the call only and may be freed on return.
+ *    "device" pointers are CUDA device memory owned by the caller; the library
+ *    never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls do not synchronise the host unless they
+ *    say so.  Outputs are valid once the stream reaches the enqueued work.
+ *  - A context (mpsa_ctx) owns the resident device data (line list, element
+ *    and species tables, FP64 population table).  A context is bound to one
+ *    device and must not be used from two host threads at once.
+ */
+#ifndef MPSA_H
+#define MPSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPSA_OK        0
+#define MPSA_EINVAL   -1   /* bad argument: shape, NaN, unsorted, out of range   */
+#define MPSA_ENOMEM   -2   /* device allocation failed                          */
+#define MPSA_ECUDA    -3   /* a CUDA runtime call failed                        */
+#define MPSA_ESTATE   -4   /* call out of order (e.g. no line list loaded)      */
+#define MPSA_ETIMEOUT -5   /* a bounded wait gave up                            */
+
+typedef struct mpsa_ctx mpsa_ctx;
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+int mpsa_create(mpsa_ctx** out, int device);
+/* Free every device buffer the context owns (synchronises the device). */
+void mpsa_destroy(mpsa_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none).  Valid until the next call. */
+const char* mpsa_last_error(void);
+/* Library version string. */
+const char* mpsa_version(void);
+
+/* Element table (host arrays of length n_elements).  Element 0 must be hydrogen
+ * (its neutral stage supplies the van der Waals perturbers n_HI).  Each element
+ * ionises once (stages I and II) with fixed partition functions U1, U2 and
+ * first ionisation energy chi_eV; log_eps is the abundance (H = 12). */
+typedef struct {
+    int32_t n_elements;
+    const double* mass_amu;
+    const double* chi_eV;
+    const double* U1;
+    const double* U2;
+    const double* log_eps;
+} mpsa_elements;
+
+/* Line list, structure of arrays (host arrays of length n_lines), sorted by
+ * ascending lambda_nm.  species[i] indexes the species table given to
+ * load_linelist.  Damping: total gamma = 10^log_gR + 10^log_gS * n_e +
+ * 10^log_gW * n_HI [s^-1] (radiative, Stark per electron, van der Waals per H I). */
+typedef struct {
+    int64_t n_lines;
+    const double* lambda_nm;
+    const float* log_gf;
+    const float* E_eV;        /* lower-level excitation energy */
+    const int32_t* species;
+    const float* log_gR;
+    const float* log_gS;
+    const float* log_gW;
+} mpsa_lines;
+
+/* Log-lambda grid lambda_j = lambda0 (1 + 1/R)^j, j = 0..N-1 with
+ * N = floor(ln(lambda1/lambda0)/ln(1+1/R)) + 1 (App. E of the paper). */
+typedef struct {
+    double lambda0_nm;
+    double lambda1_nm;
+    double R;
+} mpsa_lgrid;
+
+/* Options of the synthesis.  Zero-initialised fields take the defaults. */
+typedef struct {
+    double cut;         /* profile cut relative to the flat continuum (default 1e-3)        */
+    double kc_factor;   /* flat continuum kappa_c = kc_factor * median kappa0 (default 1e-2) */
+    int32_t precision;  /* MPSA_PREC_* (default compensated FP32)                           */
+    int32_t tile;       /* grid points per CTA tile; 0 = library default                   */
+} mpsa_synth_opts;
+
+#define MPSA_PREC_FP32_COMPENSATED 0   /* FP32 profiles, chunked FP32 partials + Kahan fold */
+#define MPSA_PREC_FP32_NAIVE       1   /* FP32 profiles, plain FP32 running sums            */
+
+/*
+ * load_linelist -- copy a line list and its species table into the context.
+ * Paper: the line lists of Sect. 2.3 / Sect. 4.4 (Kurucz, VALD); lines carry
+ * the quantities of Eq. (l_nu_line).
+ *   n_species, species_element[n_species], species_stage[n_species] (host):
+ *     species s belongs to element species_element[s] (index into the element
+ *     table of set_atmosphere_grid) in stage species_stage[s] (0 = I, 1 = II).
+ *   lines (host): the list, ascending in lambda_nm (MPSA_EINVAL otherwise).
+ * Replaces any previously loaded list.  Synchronises the device on return.
+ * Errors: MPSA_EINVAL (n_lines < 1, non-finite or unsorted lambda, species out
+ * of range), MPSA_ENOMEM, MPSA_ECUDA.
+ */
+int load_linelist(mpsa_ctx* ctx, int32_t n_species, const int32_t* species_element,
+                  const int32_t* species_stage, const mpsa_lines* lines);
+
+/*
+ * set_atmosphere_grid -- build the FP64 population table (paper Sect. 2.1 and
+ * App. A: Saha-Boltzmann populations with n_e from charge conservation).
+ *   el (host): element table.
+ *   n_points, T[n_points], P[n_points] (host): temperatures [K] and gas
+ *     pressures [dyn cm^-2] of the atmosphere points (any set, e.g. a T-P grid).
+ *   n_comp, abund_scale (host, [n_comp][n_elements] row-major, or NULL with
+ *     n_comp = 1): per-element abundance multipliers of each composition.
+ *   vturb_cm_s: micro-turbulent velocity added to the thermal Doppler width.
+ * The table holds, per (composition, point) in that order (row cp = comp *
+ * n_points + point): n_e, n_HI, rho and N/U of both stages of every element.
+ * Computed on the device in FP64 (one bisection per row).  Synchronises.
+ * Errors: MPSA_EINVAL (non-positive T or P, n_elements < 1, bad scales).
+ */
+int set_atmosphere_grid(mpsa_ctx* ctx, const mpsa_elements* el, int32_t n_points,
+                        const double* T, const double* P, int32_t n_comp,
+                        const double* abund_scale, double vturb_cm_s);
+
+/* Number of grid points N of a log-lambda grid (0 on invalid input). */
+int64_t mpsa_grid_size(const mpsa_lgrid* grid);
+
+/*
+ * synth_opacity -- line-by-line opacity on a log-lambda grid (paper Eq.
+ * l_nu_line summed over lines, Sect. 2.1; grid and cut of App. E / Sect. 4.3).
+ *   grid (host): the lambda grid, N = mpsa_grid_size(grid) points.
+ *   n_sel, sel[n_sel] (host): population-table rows cp = comp*n_points + point.
+ *   kappa_out (device, float[n_sel][N], row-major): line opacity [cm^2 g^-1].
+ *   kappa_c_out (device, float[n_sel], or NULL): the flat continuum of each row,
+ *     kappa_c = kc_factor * median over all lines of the line-centre opacity.
+ *   evals_out (device, int64[n_sel], or NULL): number of (line, grid point)
+ *     profile evaluations inside the lines' cut windows.
+ * A line contributes at grid point j iff its absorption coefficient there is
+ * >= cut * kappa_c (FP32 decision).  Profiles are evaluated in FP32 (Voigt,
+ * three-tier rational method), populations come from the FP64 table.
+ * Stream-ordered, no host synchronisation; scratch is stream-ordered device
+ * memory (cudaMallocAsync / cudaFreeAsync), released in stream order after the
+ * call's kernels.
+ * Errors: MPSA_ESTATE (no line list / grid), MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
+ */
+int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const int32_t* sel,
+                  float* kappa_out, float* kappa_c_out, int64_t* evals_out,
+                  const mpsa_synth_opts* opts, void* stream);
+
+#define MPSA_MEAN_ARITH 0
+#define MPSA_MEAN_GEOM  1
+
+/*
+ * build_odf -- opacity distribution functions (paper Sect. 2.3 and App. E):
+ * per row and interval, the values are ordered ascending, the ordered profile
+ * is split at cumulative width fractions c_s = w_1 + ... + w_s (FP64 partial
+ * sums, c_n forced to 1; a point straddling a boundary is split fractionally)
+ * and each sub-bin is replaced by its mean.
+ *   kappa (device, float[n_rows][N]): non-negative, finite values.
+ *   K, bounds[K+1] (host, int64): interval k = [bounds[k], bounds[k+1]);
+ *     strictly increasing, bounds[0] >= 0, bounds[K] <= N, each interval
+ *     shorter than 2^21 points.
+ *   n_steps, widths[n_steps] (host): sub-bin width fractions, positive, summing
+ *     to 1 within 1e-12.  n_steps <= 32.
+ *   mean_kind: MPSA_MEAN_ARITH (arithmetic mean of the sub-bin) or
+ *     MPSA_MEAN_GEOM (exp of the mean of ln kappa; zero values give 0).
+ *   odf_out (device, double[n_rows][K][n_steps]).
+ * Order statistics are found by a 4-level radix multi-select on the FP32 bit
+ * patterns with exact integer partial sums; only the final cross-exponent
+ * reduction is FP64.  Stream-ordered, no host synchronisation.
+ * Errors: MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
+ */
+int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N,
+              int32_t K, const int64_t* bounds, int32_t n_steps, const double* widths,
+              int32_t mean_kind, double* odf_out, void* stream);
+
+/* One model atmosphere for synth_spectrum (host arrays of length n_depth,
+ * ordered from the top down): column mass m [g cm^-2], T [K], P [dyn cm^-2]. */
+typedef struct {
+    int32_t n_depth;
+    const double* m;
+    const double* T;
+    const double* P;
+    int32_t comp;      /* composition row of the atmosphere grid's abundance scales */
+} mpsa_atmos;
+
+/*
+ * synth_spectrum -- emergent intensity I(mu, lambda) of one atmosphere over a
+ * wavelength window (paper Eq. Ilambda with LTE source S = B_lambda(T)).
+ * For every depth the populations, the line opacity on the window grid (same
+ * cut rule as synth_opacity, lines centred outside the window contribute their
+ * wings) and the flat continuum are built; tau follows by the trapezoid rule in
+ * column mass and I by a linear-source integration from a diffusion lower
+ * boundary (I = S + mu dS/dtau) to the surface.
+ *   atm (host), win (host): the atmosphere and the window grid (N_win points).
+ *   n_mu, mu[n_mu] (host): direction cosines in (0, 1].
+ *   I_out (device, float[n_mu][N_win]).
+ * Requires the element table of set_atmosphere_grid (the atmosphere's own
+ * populations are computed in FP64 on the device).  Stream-ordered.
+ * Errors: MPSA_ESTATE, MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
+ */
+int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_lgrid* win,
+                   int32_t n_mu, const double* mu, float* I_out,
+                   const mpsa_synth_opts* opts, void* stream);
+
+/*
+ * Kernel timing for measurement tools (not part of the method).  While enabled,
+ * the library records a CUDA event pair on the launching stream around each
+ * launch of its two dominant kernels: MPSA_KERNEL_PROFILE (the profile kernel
+ * of synth_opacity / synth_spectrum) and MPSA_KERNEL_ODF (the kernel of
+ * build_odf).  mpsa_profile_read waits for the recorded events, returns the
+ * summed device time [ms] and launch count of one kernel, and clears its list.
+ * Do not enable while capturing a CUDA graph.
+ */
+#define MPSA_KERNEL_PROFILE 0
+#define MPSA_KERNEL_ODF     1
+int mpsa_profile_enable(mpsa_ctx* ctx, int enable);
+int mpsa_profile_read(mpsa_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPSA_H */

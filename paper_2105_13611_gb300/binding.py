@@ -1,0 +1,216 @@
+"""ctypes binding of the C ABI in include/mpsa.h (argument marshalling only).
+
+Host arrays are numpy arrays; device buffers are torch CUDA tensors whose data
+pointers are passed through.  Every call runs in the CUDA library; a missing
+library raises instead of falling back to any CPU code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmpsa.so")
+
+MPSA_OK, MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA, MPSA_ESTATE, MPSA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+PREC_FP32_COMPENSATED, PREC_FP32_NAIVE = 0, 1
+MEAN_ARITH, MEAN_GEOM = 0, 1
+
+EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "mpsa_grid_size",
+            "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
+            "mpsa_profile_enable", "mpsa_profile_read"]
+KERNEL_PROFILE, KERNEL_ODF = 0, 1
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+
+
+class Elements(C.Structure):
+    _fields_ = [("n_elements", C.c_int32), ("mass_amu", _dp), ("chi_eV", _dp), ("U1", _dp), ("U2", _dp),
+                ("log_eps", _dp)]
+
+
+class Lines(C.Structure):
+    _fields_ = [("n_lines", C.c_int64), ("lambda_nm", _dp), ("log_gf", _fp), ("E_eV", _fp), ("species", _ip),
+                ("log_gR", _fp), ("log_gS", _fp), ("log_gW", _fp)]
+
+
+class LGrid(C.Structure):
+    _fields_ = [("lambda0_nm", C.c_double), ("lambda1_nm", C.c_double), ("R", C.c_double)]
+
+
+class SynthOpts(C.Structure):
+    _fields_ = [("cut", C.c_double), ("kc_factor", C.c_double), ("precision", C.c_int32), ("tile", C.c_int32)]
+
+
+class Atmos(C.Structure):
+    _fields_ = [("n_depth", C.c_int32), ("m", _dp), ("T", _dp), ("P", _dp), ("comp", C.c_int32)]
+
+
+class MpsaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mpsa error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmpsa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run paper_2105_13611_gb300/build.py (no CPU fallback)")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.mpsa_create.argtypes = [C.POINTER(vp), C.c_int]
+    lib.mpsa_destroy.argtypes = [vp]
+    lib.mpsa_destroy.restype = None
+    lib.mpsa_last_error.restype = C.c_char_p
+    lib.mpsa_version.restype = C.c_char_p
+    lib.mpsa_grid_size.argtypes = [C.POINTER(LGrid)]
+    lib.mpsa_grid_size.restype = C.c_int64
+    lib.load_linelist.argtypes = [vp, C.c_int32, _ip, _ip, C.POINTER(Lines)]
+    lib.set_atmosphere_grid.argtypes = [vp, C.POINTER(Elements), C.c_int32, _dp, _dp, C.c_int32, _dp, C.c_double]
+    lib.synth_opacity.argtypes = [vp, C.POINTER(LGrid), C.c_int32, _ip, vp, vp, vp, C.POINTER(SynthOpts), vp]
+    lib.build_odf.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.c_int32, _dp,
+                              C.c_int32, vp, vp]
+    lib.synth_spectrum.argtypes = [vp, C.POINTER(Atmos), C.POINTER(LGrid), C.c_int32, _dp, vp,
+                                   C.POINTER(SynthOpts), vp]
+    lib.mpsa_profile_enable.argtypes = [vp, C.c_int]
+    lib.mpsa_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    for f in ("mpsa_create", "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
+              "mpsa_profile_enable", "mpsa_profile_read"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != MPSA_OK:
+        raise MpsaError(rc, _lib.mpsa_last_error().decode())
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _dev(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def grid_size(lam0_nm, lam1_nm, R) -> int:
+    lib = load_library()
+    return int(lib.mpsa_grid_size(C.byref(LGrid(lam0_nm, lam1_nm, R))))
+
+
+def make_opts(cut=1e-3, kc_factor=1e-2, precision=PREC_FP32_COMPENSATED):
+    return SynthOpts(cut, kc_factor, precision, 0)
+
+
+class Context:
+    """One mpsa_ctx on one CUDA device: resident line list and population table."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        _check(self.lib.mpsa_create(C.byref(h), int(device)))
+        self.h = h
+        self.device = device
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            self.lib.mpsa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile_enable(self, on=True):
+        _check(self.lib.mpsa_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, kernel):
+        """(total device ms, launches) of KERNEL_PROFILE or KERNEL_ODF since the last read."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(self.lib.mpsa_profile_read(self.h, kernel, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def load_linelist(self, lines, species_element, species_stage):
+        """lines: workloads.LineList (or any object with the same fields)."""
+        se = _arr(species_element, np.int32)
+        ss = _arr(species_stage, np.int32)
+        f = dict(lam=_arr(lines.lam_nm, np.float64), gf=_arr(lines.log_gf, np.float32), E=_arr(lines.E_eV, np.float32),
+                 sp=_arr(lines.species, np.int32), R=_arr(lines.log_gR, np.float32), S=_arr(lines.log_gS, np.float32),
+                 W=_arr(lines.log_gW, np.float32))
+        L = Lines(len(f["lam"]), _ptr(f["lam"], C.c_double), _ptr(f["gf"], C.c_float), _ptr(f["E"], C.c_float),
+                  _ptr(f["sp"], C.c_int32), _ptr(f["R"], C.c_float), _ptr(f["S"], C.c_float), _ptr(f["W"], C.c_float))
+        _check(self.lib.load_linelist(self.h, len(se), _ptr(se, C.c_int32), _ptr(ss, C.c_int32), C.byref(L)))
+
+    def set_atmosphere_grid(self, el, T, P, abund_scale=None, vturb=0.0):
+        """el: workloads.Elements; T, P: arrays of the atmosphere points; abund_scale [n_comp][n_el] or None."""
+        arrs = [_arr(el.mass_amu, np.float64), _arr(el.chi_eV, np.float64), _arr(el.U1, np.float64),
+                _arr(el.U2, np.float64), _arr(el.log_eps, np.float64)]
+        E = Elements(len(arrs[0]), *[_ptr(a, C.c_double) for a in arrs])
+        T = _arr(T, np.float64)
+        P = _arr(P, np.float64)
+        if abund_scale is None:
+            n_comp, ab = 1, None
+        else:
+            ab = _arr(abund_scale, np.float64)
+            n_comp = ab.shape[0]
+        _check(self.lib.set_atmosphere_grid(self.h, C.byref(E), len(T), _ptr(T, C.c_double), _ptr(P, C.c_double),
+                                            n_comp, _ptr(ab, C.c_double) if ab is not None else None, float(vturb)))
+        self.n_points = len(T)
+
+    def synth_opacity(self, grid, sel, kappa_out, kappa_c_out=None, evals_out=None, opts=None, stream=None):
+        s = _arr(sel, np.int32)
+        g = LGrid(grid.lam0_nm, grid.lam1_nm, grid.R)
+        o = opts if opts is not None else make_opts()
+        _check(self.lib.synth_opacity(self.h, C.byref(g), len(s), _ptr(s, C.c_int32), _dev(kappa_out),
+                                      _dev(kappa_c_out), _dev(evals_out), C.byref(o), _stream(stream)))
+
+    def build_odf(self, kappa, bounds, widths, odf_out, mean_kind=MEAN_ARITH, stream=None):
+        b = _arr(bounds, np.int64)
+        w = _arr(widths, np.float64)
+        n_rows, N = kappa.shape
+        _check(self.lib.build_odf(self.h, _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
+                                  _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream)))
+
+    def synth_spectrum(self, m, T, P, win, mus, I_out, comp=0, opts=None, stream=None):
+        m = _arr(m, np.float64)
+        T = _arr(T, np.float64)
+        P = _arr(P, np.float64)
+        mu = _arr(mus, np.float64)
+        a = Atmos(len(m), _ptr(m, C.c_double), _ptr(T, C.c_double), _ptr(P, C.c_double), int(comp))
+        g = LGrid(win.lam0_nm, win.lam1_nm, win.R)
+        o = opts if opts is not None else make_opts()
+        _check(self.lib.synth_spectrum(self.h, C.byref(a), C.byref(g), len(mu), _ptr(mu, C.c_double), _dev(I_out),
+                                       C.byref(o), _stream(stream)))

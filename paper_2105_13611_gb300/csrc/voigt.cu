@@ -1,0 +1,75 @@
+// Host-side set-up of the Voigt constants: 12-point Gauss-Hermite nodes and
+// weights computed from the Hermite polynomials, then the shifted-contour
+// coefficients of Humlicek (1979).  FP64 on the host, copied once per device.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "voigt.cuh"
+
+namespace mpsa {
+
+namespace {
+
+// Physicists' Hermite polynomial H_n(x) and H_{n-1}(x) by the three-term recurrence
+// H_{k+1} = 2x H_k - 2k H_{k-1}.
+void hermite(int n, double x, double* hn, double* hn1) {
+    double h0 = 1.0, h1 = 2.0 * x;
+    if (n == 0) { *hn = h0; *hn1 = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double h2 = 2.0 * x * h1 - 2.0 * k * h0;
+        h0 = h1;
+        h1 = h2;
+    }
+    *hn = h1;
+    *hn1 = h0;
+}
+
+}  // namespace
+
+int voigt_host_consts(VoigtConsts* out) {
+    const int n = 2 * kGHPairs;
+    double nodes[kGHPairs], weights[kGHPairs];
+    int found = 0;
+    // The positive roots of H_n lie in (0, sqrt(2n+1)); bracket sign changes on a
+    // fine scan, then bisect to full precision.
+    const double xmax = sqrt(2.0 * n + 1.0) + 1.0;
+    const int steps = 20000;
+    double xprev = 1e-9, hprev, dummy;
+    hermite(n, xprev, &hprev, &dummy);
+    for (int i = 1; i <= steps && found < kGHPairs; ++i) {
+        double x = xmax * i / steps, h;
+        hermite(n, x, &h, &dummy);
+        if ((h > 0) != (hprev > 0)) {
+            double lo = xprev, hi = x, hlo = hprev;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi), hm;
+                hermite(n, mid, &hm, &dummy);
+                if ((hm > 0) == (hlo > 0)) { lo = mid; hlo = hm; } else { hi = mid; }
+            }
+            nodes[found++] = 0.5 * (lo + hi);
+        }
+        xprev = x;
+        hprev = h;
+    }
+    if (found != kGHPairs) return fail(MPSA_EINVAL, "voigt_init: found %d Hermite roots", found);
+    // omega_k = 2^{n-1} n! sqrt(pi) / (n^2 H_{n-1}(x_k)^2)
+    double fact = 1.0;
+    for (int k = 2; k <= n; ++k) fact *= k;
+    for (int k = 0; k < kGHPairs; ++k) {
+        double hn, hn1;
+        hermite(n, nodes[k], &hn, &hn1);
+        weights[k] = pow(2.0, n - 1) * fact * sqrt(kPI) / ((double)n * n * hn1 * hn1);
+    }
+    VoigtConsts& h = *out;
+    const double dl = (double)kGHDelta;
+    const double pre = exp(dl * dl) / kPI;
+    for (int k = 0; k < kGHPairs; ++k) {
+        h.s[k] = (float)nodes[k];
+        h.U[k] = (float)(pre * weights[k] * cos(2.0 * dl * nodes[k]));
+        h.S[k] = (float)(pre * weights[k] * sin(2.0 * dl * nodes[k]));
+    }
+    return MPSA_OK;
+}
+
+}  // namespace mpsa

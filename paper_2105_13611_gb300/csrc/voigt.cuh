@@ -1,0 +1,128 @@
+// FP32 Voigt function H(v, a) = Re w(v + i a) for the profile of Eq. (l_nu_line).
+//
+// Three tiers, chosen per point by |z|^2 = v^2 + a^2 (the reasoning and the
+// measured error bounds are in the design doc):
+//
+//  far   |z|^2 >= 1600: the one-level Laplace continued fraction
+//        w ~ (i/sqrt(pi)) / (z - 1/(2z)) with its real part written out:
+//        H = (a/sqrt(pi)) y (2 + 4y) / (1 + 8 a^2 y^2),  y = 1/(2|z|^2 - 1).
+//        Relative error <= 1.2e-6; one reciprocal, no cancellation.
+//  mid   36 <= |z|^2 < 1600: the Laplace continued fraction with five levels
+//        (partial numerators 5/2, 2, 3/2, 1, 1/2) evaluated bottom-up on
+//        separate real and imaginary parts.  The imaginary part of every level
+//        is a sum of positive terms, so H = Im t / (sqrt(pi) |t|^2) keeps full
+//        relative accuracy even for tiny a.  exp(-v^2) is added for a < 1e-2,
+//        where the fraction omits the Gaussian core.
+//  core  |z|^2 < 36: Humlicek's (1979) shifted-contour Gauss-Hermite sum.
+//        Shifting the integration path of w(z) = (i/pi) int e^{-t^2}/(z-t) dt
+//        by delta = 1.5 below the real axis and applying 12-point Gauss-Hermite
+//        quadrature gives w(z) ~ sum_k c_k /(z + i delta - s_k) with
+//        c_k = (i/pi) e^{delta^2} omega_k e^{2 i delta s_k}.  For a >= 2 the real
+//        part of the sum is used directly ("region I"); for a < 2 the exact
+//        exp(-v^2) is taken for the real axis and only the a-dependent part
+//        Re[R(z) - R(v)] comes from the sum, written with an explicit factor a
+//        ("region II").  The constants are computed on the host from the
+//        Hermite nodes and weights (mpsa::voigt_init).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpsa {
+
+constexpr int kGHPairs = 6;          // 12-point Gauss-Hermite, symmetric pairs
+constexpr float kGHDelta = 1.5f;     // contour shift
+constexpr float kInvSqrtPi = 0.56418958354775628f;
+
+struct VoigtConsts {
+    float s[kGHPairs];   // positive Hermite nodes
+    float U[kGHPairs];   // e^{delta^2}/pi * omega_k * cos(2 delta s_k)
+    float S[kGHPairs];   // e^{delta^2}/pi * omega_k * sin(2 delta s_k)
+};
+
+// Host: the constants from the Hermite nodes and weights (voigt.cu).
+int voigt_host_consts(VoigtConsts* out);
+
+// Every translation unit that evaluates H keeps its own copy of the constants;
+// it uploads them with voigt_upload() once per device before its first launch.
+static __constant__ VoigtConsts c_voigt;
+
+static inline int voigt_upload() {
+    VoigtConsts h;
+    int rc = voigt_host_consts(&h);
+    if (rc != MPSA_OK) return rc;
+    cudaError_t e = cudaMemcpyToSymbol(c_voigt, &h, sizeof(h));
+    return e == cudaSuccess ? MPSA_OK : fail(MPSA_ECUDA, "cudaMemcpyToSymbol(c_voigt): %s", cudaGetErrorString(e));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// far tier.  V = v^2, A = a^2, ka = a/sqrt(pi).
+__device__ __forceinline__ float voigt_far(float V, float A, float ka) {
+    float y = rcp_approx(fmaf(2.f, V, fmaf(2.f, A, -1.f)));
+    float e = 8.f * A * y * y;
+    return ka * y * fmaf(4.f, y, 2.f) * fmaf(e, e - 1.f, 1.f);
+}
+
+// mid tier (five continued-fraction levels).
+__device__ __forceinline__ float voigt_mid(float v, float a) {
+    float tr = v, ti = a;
+#pragma unroll
+    for (int k = 5; k >= 1; --k) {
+        const float c = 0.5f * (float)k;
+        float cm = c * rcp_approx(fmaf(tr, tr, ti * ti));
+        float ntr = fmaf(-cm, tr, v);
+        ti = fmaf(cm, ti, a);
+        tr = ntr;
+    }
+    float h = kInvSqrtPi * ti * rcp_approx(fmaf(tr, tr, ti * ti));
+    if (a < 1e-2f) h += expf(-v * v);
+    return h;
+}
+
+// core tier (shifted Gauss-Hermite, regions I and II).
+__device__ __forceinline__ float voigt_core(float v, float a) {
+    const float d = kGHDelta;
+    const float Y1 = a + d, Y12 = Y1 * Y1;
+    float sum = 0.f;
+    if (a < 2.f) {
+        const float dY = Y1 * d, Yd = Y1 + d, d2 = d * d;
+#pragma unroll
+        for (int k = 0; k < kGHPairs; ++k) {
+            const float sk = c_voigt.s[k], Uk = c_voigt.U[k], Sk = c_voigt.S[k];
+            float r = v - sk, rp = v + sk;
+            float r2 = r * r, rp2 = rp * rp;
+            float p1 = (r2 + d2) * (r2 + Y12);
+            float p2 = (rp2 + d2) * (rp2 + Y12);
+            float t1 = fmaf(Uk, r2 - dY, Sk * r * Yd);
+            float t2 = fmaf(Uk, rp2 - dY, -Sk * rp * Yd);
+            sum = fmaf(fmaf(t1, p2, t2 * p1), rcp_approx(p1 * p2), sum);
+        }
+        return fmaf(a, sum, expf(-v * v));
+    }
+#pragma unroll
+    for (int k = 0; k < kGHPairs; ++k) {
+        const float sk = c_voigt.s[k], Uk = c_voigt.U[k], Sk = c_voigt.S[k];
+        float r = v - sk, rp = v + sk;
+        float q1 = fmaf(r, r, Y12), q2 = fmaf(rp, rp, Y12);
+        float UY = Uk * Y1;
+        sum = fmaf(fmaf(q2, fmaf(-Sk, r, UY), q1 * fmaf(Sk, rp, UY)), rcp_approx(q1 * q2), sum);
+    }
+    return sum;
+}
+
+// H(v, a) for any v (sign ignored) and a > 0.
+__device__ __forceinline__ float voigt_H(float v, float a) {
+    v = fabsf(v);
+    const float V = v * v, A = a * a, Z = V + A;
+    if (Z >= 1600.f) return voigt_far(V, A, a * kInvSqrtPi);
+    if (Z >= 36.f) return voigt_mid(v, a);
+    return voigt_core(v, a);
+}
+
+}  // namespace mpsa

@@ -1,0 +1,84 @@
+"""GPU parity of build_odf against the FP64 oracle ODF (through the C ABI)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import odf as od
+from oracle import synthesis as sy
+
+from gpu_util import ODF_RTOL, gpu_context, gpu_synth
+
+pytestmark = pytest.mark.gpu
+W12 = wl.ODF_WIDTHS_12
+
+
+def gpu_odf(kappa_np, bounds, widths):
+    import torch
+    from paper_2105_13611_gb300 import binding
+    ctx = binding.Context(0)
+    k = torch.from_numpy(np.ascontiguousarray(kappa_np, dtype=np.float32)).cuda()
+    if k.ndim == 1:
+        k = k[None, :]
+    out = torch.empty((k.shape[0], len(bounds) - 1, len(widths)), dtype=torch.float64, device="cuda")
+    ctx.build_odf(k, bounds, widths, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check(kappa, bounds, widths, rtol=ODF_RTOL):
+    kappa = np.asarray(kappa, dtype=np.float32)
+    g = gpu_odf(kappa, bounds, widths)
+    rows = kappa[None, :] if kappa.ndim == 1 else kappa
+    for r in range(rows.shape[0]):
+        o = od.odf(rows[r].astype(np.float64), bounds, widths)
+        scale = np.maximum(np.abs(o), 1e-300)
+        rel = np.abs(g[r] - o) / scale
+        ok = (rel <= rtol) | ((o == 0) & (g[r] == 0))
+        assert ok.all(), (r, np.argwhere(~ok)[:5], g[r][~ok][:5], o[~ok][:5])
+    return g
+
+
+def test_random_lognormal_intervals():
+    rng = np.random.default_rng(1)
+    x = rng.lognormal(0, 5, (3, 100_003))
+    g = check(x, wl.equal_intervals(100_003, 7), W12)
+    assert np.all(np.diff(g, axis=2) >= 0)
+
+
+def test_adversarial():
+    n = 5000
+    rng = np.random.default_rng(2)
+    cases = [np.zeros(n), np.full(n, 3.5), np.r_[np.zeros(n - 1), 1e30], np.repeat([1.0, 2.0, 3.0], [2000, 1, 2999]),
+             np.r_[np.zeros(n // 2), np.ones(n - n // 2)], rng.integers(0, 3, n).astype(float),
+             np.r_[1e-40 * np.ones(100), rng.lognormal(0, 1, n - 100)],          # denormals
+             rng.lognormal(-80, 10, n)]                                          # very small and wide
+    for x in cases:
+        check(x, [0, n], W12)
+
+
+def test_small_and_ragged_intervals():
+    rng = np.random.default_rng(3)
+    x = rng.lognormal(0, 2, 1000)
+    for b in ([0, 1], [0, 5, 11, 12, 13, 40, 1000], [3, 997]):
+        check(x, b, W12)
+    check(x, [0, 1000], [0.5, 0.5])
+    check(x, [0, 1000], [1.0])
+    check(x, [0, 1000], np.full(32, 1 / 32))
+
+
+def test_synthesised_opacity_odf():
+    # ODF of the GPU's own opacity against the oracle ODF of the same FP32 array (<= 1e-5),
+    # and end to end against the oracle opacity (order statistics inherit the opacity bound 1e-4)
+    w = wl.config_tiny(n_lines=400, lam=(300.0, 303.1), seed=8)
+    ctx, L = gpu_context(w)
+    kg, kcg, _ = gpu_synth(ctx, w, np.arange(4))
+    b = wl.equal_intervals(kg.shape[1], 5)
+    g = check(kg, b, W12)
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    for s in range(4):
+        pl = sy.prepare(L, se, ss, el, w.T[s], w.P[s], w.grid)
+        k, slack, W = sy.kappa_dense(pl)
+        o = od.odf(k, b, W12)
+        rel = np.abs(g[s] - o) / (o + pl.kappa_c)
+        assert rel.max() <= 1e-4 + (slack.max() / pl.kappa_c if slack.max() > 0 else 0)

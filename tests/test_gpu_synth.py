@@ -1,0 +1,100 @@
+"""GPU parity of synth_opacity against the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import synthesis as sy
+
+from gpu_util import gpu_context, gpu_synth, opacity_violations, rel_report
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_dense(w, L, T, P, abund=None):
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    pl = sy.prepare(L, se, ss, el, T, P, w.grid, w.cut, w.kc_factor, abund_scale=abund)
+    k, slack, W = sy.kappa_dense(pl)
+    return pl, k, slack, W
+
+
+@pytest.mark.parametrize("n_lines,lam,seed", [(40, (300.0, 300.6), 7), (400, (300.0, 303.1), 8), (3, (500.0, 500.2), 9)])
+def test_dense_parity_small(n_lines, lam, seed):
+    # several 2048-point tiles with a ragged tail, all four (T, P) points at once
+    w = wl.config_tiny(n_lines=n_lines, lam=lam, seed=seed)
+    ctx, L = gpu_context(w)
+    sel = np.arange(len(w.T))
+    kg, kcg, evg = gpu_synth(ctx, w, sel)
+    for s in sel:
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        assert abs(kcg[s] / pl.kappa_c - 1) < 1e-5
+        bad, err, bound = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (s, bad[:10], err[bad[:10]], bound[bad[:10]], rel_report(kg[s], k, pl.kappa_c))
+        # evaluations: outer windows include at most 4 padding points per line
+        assert W <= evg[s] <= W + 8 * n_lines + 16
+
+
+def test_precision_naive_runs_and_agrees():
+    w = wl.config_tiny(n_lines=200, lam=(300.0, 301.0), seed=12)
+    ctx, L = gpu_context(w)
+    kc_, _, _ = gpu_synth(ctx, w, [1], precision=0)
+    kn_, _, _ = gpu_synth(ctx, w, [1], precision=1)
+    pl, k, slack, W = oracle_dense(w, L, w.T[1], w.P[1])
+    bad, _, _ = opacity_violations(kn_[0], k, pl.kappa_c, slack)
+    assert len(bad) == 0
+    assert np.array_equal(kc_[0] > 0, kn_[0] > 0)
+
+
+def test_compositions_and_row_selection():
+    # abundance scales per element; rows selected out of order from a 2-composition table
+    w = wl.config_tiny(n_lines=120, lam=(300.0, 300.8), seed=13)
+    ab = wl.abundance_scales(2, wl.elements(w.n_metals).n, seed=5)
+    ctx, L = gpu_context(w, abund=ab)
+    nP = len(w.T)
+    sel = [1 * nP + 2, 0 * nP + 0, 1 * nP + 3]
+    kg, kcg, _ = gpu_synth(ctx, w, sel)
+    for r, cp in enumerate(sel):
+        comp, p = divmod(cp, nP)
+        pl, k, slack, W = oracle_dense(w, L, w.T[p], w.P[p], abund=ab[comp])
+        assert abs(kcg[r] / pl.kappa_c - 1) < 1e-5
+        bad, _, _ = opacity_violations(kg[r], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (r, bad[:5])
+
+
+def test_extreme_damping_and_pressures():
+    # high pressure (Lorentzian, a >> 1) and low pressure (a << 1e-6) rows
+    w = wl.config_tiny(n_lines=60, lam=(400.0, 400.5), seed=14)
+    w.T = np.array([2000.0, 3000.0, 50000.0, 200000.0])
+    w.P = np.array([1e8, 1e-4, 1e8, 1e-4])
+    ctx, L = gpu_context(w)
+    kg, kcg, _ = gpu_synth(ctx, w, np.arange(4))
+    for s in range(4):
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        assert abs(kcg[s] / pl.kappa_c - 1) < 2e-5
+        bad, err, bound = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
+
+
+def test_full_size_sampled():
+    # the 20,000-line, 575,365-point, 4-point workload in the launch configuration of the benchmark;
+    # the oracle evaluates sampled grid points one by one (random points and the cores of strong lines)
+    w = wl.config_small()
+    ctx, L = gpu_context(w)
+    kg, kcg, evg = gpu_synth(ctx, w, np.arange(4))
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    rng = np.random.default_rng(0)
+    for s in range(4):
+        pl = sy.prepare(L, se, ss, el, w.T[s], w.P[s], w.grid, w.cut, w.kc_factor)
+        assert abs(kcg[s] / pl.kappa_c - 1) < 1e-5
+        strong = np.argsort(pl.kappa0)[-40:]
+        lnq = np.log1p(1 / w.grid.R)
+        centres = np.round(np.log(L.lam_nm[strong] / w.grid.lam0_nm) / lnq).astype(np.int64)
+        js = np.unique(np.clip(np.r_[rng.integers(0, pl.N, 150), centres, centres + 3, centres - 17], 0, pl.N - 1))
+        ko, so = sy.kappa_at(pl, js)
+        bad, err, bound = opacity_violations(kg[s][js], ko, pl.kappa_c, so)
+        assert len(bad) == 0, (s, js[bad[:5]], rel_report(kg[s][js], ko, pl.kappa_c))
+        assert np.all(np.isfinite(kg[s])) and np.all(kg[s] >= 0)
+        lo, hi = sy.windows(pl)
+        W = int(np.sum(np.maximum(hi - lo + 1, 0)))
+        assert W <= evg[s] <= W + 8 * len(L)
