@@ -49,19 +49,29 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
-    p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank")
+    p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank (table workload)")
+    p.add_argument("--workload", choices=["table", "small"], default="table",
+                   help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
 
+# Rows (T index * 25 + P index) of the 57 x 25 table taken by one step, in increasing
+# cost.  They sit at the 6, 19, 31, 44, 56, 69, 81 and 94 % quantiles of the per-row
+# evaluation count W over all 1425 rows (W estimated once from a 20,000-line
+# subsample of the same list): W per row from 1.6e10 to 1.4e13, about 2.2e13 per
+# step, i.e. a cross-section of the table's cost distribution.
+TABLE_ROWS = [277, 879, 232, 964, 1354, 1044, 1321, 297]
+
+
 def batch_points(rank: int, B: int):
-    """A fixed stratified batch of the 57 x 25 table for each rank: T and P indices
-    spread over the whole grid (Latin-hypercube style), shifted per rank."""
-    rng = np.random.default_rng(4242 + rank)
-    ti = (np.linspace(2, 54, B).round().astype(int) + rank * 3) % 57
-    pi = rng.permutation(np.linspace(1, 23, B).round().astype(int))
-    return (ti * 25 + pi).astype(np.int32)
+    """The first B rows of TABLE_ROWS; rank r shifts every row's temperature index by r."""
+    if not 1 <= B <= len(TABLE_ROWS):
+        raise ValueError(f"--batch must be 1..{len(TABLE_ROWS)}")
+    rows = np.array(TABLE_ROWS[:B], dtype=np.int64)
+    ti, pi = rows // 25, rows % 25
+    return (((ti + rank) % 57) * 25 + pi).astype(np.int32)
 
 
 class Clocks:
@@ -133,7 +143,8 @@ def oracle_sample(seconds: float, w, lines, row_T, row_P):
     evals, t_total, n_slices = 0, 0.0, 0
     t_start = time.perf_counter()
     while time.perf_counter() - t_start < seconds:
-        lam0 = float(np.exp(rng.uniform(math.log(200.0), math.log(2000.0))))
+        lo, hi = max(200.0, w.grid.lam0_nm), min(2000.0, w.grid.lam1_nm - 0.2)
+        lam0 = float(np.exp(rng.uniform(math.log(lo), math.log(hi))))
         lam1 = lam0 + 0.2
         i0, i1 = np.searchsorted(lines.lam_nm, [lam0, lam1])
         if i1 - i0 < 2:
@@ -147,7 +158,7 @@ def oracle_sample(seconds: float, w, lines, row_T, row_P):
         t_total += time.perf_counter() - t0
         evals += W
         n_slices += 1
-    desc = (f"{n_slices} slices of 0.2 nm (lines of the 5e6-line list inside each slice, dense FP64 synthesis "
+    desc = (f"{n_slices} slices of 0.2 nm (lines of the {len(lines)}-line list inside each slice, dense FP64 synthesis "
             f"on the slice grid at R=2e6 and T={row_T:.0f} K, P={row_P:.3g}, plus the slice ODF)")
     return evals / t_total, evals, t_total, desc
 
@@ -156,9 +167,9 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = wl.config_table()
+    w = wl.config_table() if args.workload == "table" else wl.config_small()
     lines = w.lines()
-    pts = batch_points(0, args.batch)
+    pts = batch_points(0, args.batch) if args.workload == "table" else np.arange(len(w.T))
     T, P = w.T[pts[0]], w.P[pts[0]]
     per_step = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
@@ -214,7 +225,7 @@ def native_arm(args):
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
-    w = wl.config_table()
+    w = wl.config_table() if args.workload == "table" else wl.config_small()
     lines = w.lines()
     el = wl.elements(w.n_metals)
     se, ss = wl.species_table(w.n_metals)
@@ -224,14 +235,14 @@ def native_arm(args):
     N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
     K = w.n_intervals
     bounds = wl.equal_intervals(N, K)
-    sel = batch_points(rank, args.batch)
+    sel = batch_points(rank, args.batch) if args.workload == "table" else np.arange(len(w.T), dtype=np.int32)
     B = len(sel)
     stream = torch.cuda.current_stream()
     kap = torch.empty((B, N), dtype=torch.float32, device=dev)
     kc = torch.empty(B, dtype=torch.float32, device=dev)
     ev = torch.empty(B, dtype=torch.int64, device=dev)
     ev_tot = torch.zeros(B, dtype=torch.int64, device=dev)
-    odf = torch.empty((B, K, 12), dtype=torch.float64, device=dev)
+    odf = torch.empty((B, K, len(w.widths)), dtype=torch.float64, device=dev)
     opts = binding.make_opts(w.cut, w.kc_factor)
 
     def step():
@@ -270,7 +281,7 @@ def native_arm(args):
     if not args.no_e2e:
         Tb = np.ascontiguousarray(w.T[sel])
         Pb = np.ascontiguousarray(w.P[sel])
-        odf_h = torch.empty((B, K, 12), dtype=torch.float64, pin_memory=True)
+        odf_h = torch.empty((B, K, len(w.widths)), dtype=torch.float64, pin_memory=True)
         kc_h = torch.empty(B, dtype=torch.float32, pin_memory=True)
         ev_h = torch.empty(B, dtype=torch.int64, pin_memory=True)
         rows = np.arange(B, dtype=np.int32)
@@ -289,9 +300,10 @@ def native_arm(args):
 
         e2e_step()
         barrier()
+        n_e2e = min(args.steps, 2)
         t0 = time.perf_counter()
         ev_e2e = 0
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             ev_e2e += e2e_step()
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
@@ -302,6 +314,7 @@ def native_arm(args):
                + bounds.nbytes + 8 * (2 * len(w.widths) + 1))          # build_odf bounds and widths
         d2h = odf_h.numel() * 8 + kc_h.numel() * 4 + ev_h.numel() * 8
         e2e = {"value": ev_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": n_e2e,
                "note": "line list resident (loaded once); per step: populations from host T, P, synthesis, ODF, "
                        "ODF table + kappa_c + evaluation counts copied to pinned host memory"}
         ctx2.close()
@@ -340,7 +353,8 @@ def native_arm(args):
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": w.name, "lines": len(lines), "species": w.n_species, "grid_points": N,
-                      "R": w.grid.R, "lambda_nm": [w.grid.lam0_nm, w.grid.lam1_nm], "tp_grid": "57 T x 25 P",
+                      "R": w.grid.R, "lambda_nm": [w.grid.lam0_nm, w.grid.lam1_nm],
+                      "tp_grid": "57 T x 25 P" if args.workload == "table" else "4 points, log P = 4",
                       "points_per_step_per_rank": B, "rows": [int(x) for x in sel], "intervals": K, "odf_steps": 12,
                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"independent points x{world}"},
            "odf_points_per_s": odf_pts, "evals_per_step": evals / args.steps,
