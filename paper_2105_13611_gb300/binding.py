@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libmpsa.so")
+LIB_PATH = os.environ.get("MPSA_LIBRARY") or os.path.join(HERE, "_lib", "libmpsa.so")
 
 MPSA_OK, MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA, MPSA_ESTATE, MPSA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PREC_FP32_COMPENSATED, PREC_FP32_NAIVE = 0, 1

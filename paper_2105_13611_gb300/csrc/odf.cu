@@ -4,18 +4,21 @@
 // boundaries and the sums of all values below them, then forms the step means
 //   m_s = (S(c_s n) - S(c_{s-1} n)) / (w_s n),
 //   S(u) = sum of the floor(u) smallest values + (u - floor(u)) * x_(floor(u)).
-// S(k) for an order statistic theta = x_(k) is sum_{x < theta} x + (k - #{x < theta}) theta.
+// For an order statistic theta = x_(k): S(k) = sum_{x < theta} x + (k - #{x < theta}) theta.
 //
 // Order statistics: MSB radix multi-select on the FP32 bit patterns (values are
-// non-negative, so the bit order is the value order), four levels of 11, 8, 8
-// and 4 bits (bits 30..20, 19..12, 11..4, 3..0).  Every histogram bin carries,
-// in one 64-bit shared-memory atomic, the count (high 24 bits) and the sum of the
-// bits below the bin's prefix (low 40 bits).  Values that share the exponent E
-// are integers in units of 2^(max(E,1)-150), so every partial sum inside an
-// exponent group is exact integer arithmetic; only the sum across exponent
-// groups (256 of them) is done in FP64.  Pass 1 reads the interval from HBM;
-// passes 2-4 re-read it (from L2) and histogram only the values whose prefix
-// matches a target's.  Zeros are counted in registers (no atomics).
+// non-negative, so the bit order is the value order) over four levels of 11, 8, 8
+// and 4 bits (bits 30..20, 19..12, 11..4, 3..0).  Every histogram bin carries the
+// count (high 24 bits) and the sum of the bits below the bin's prefix (low 40
+// bits) in one 64-bit shared-memory atomic.  Values of one exponent E are integers
+// in units of 2^(max(E,1)-150), so every partial sum inside an exponent group is
+// exact integer arithmetic; only the sum across the 256 exponent groups is FP64.
+//
+// Passes over the interval: pass 1 (from HBM, 16-byte vector loads) builds the
+// level-1 histogram; pass 2 (from L2) copies the values that fall into a target's
+// level-1 bin into a shared-memory candidate buffer; levels 2-4 then run on that
+// buffer.  If the candidates do not fit, levels 2-4 re-read the interval instead.
+// Zeros are counted in registers and never enter atomics or the buffer.
 #include <math.h>
 #include <string.h>
 
@@ -27,58 +30,180 @@ namespace mpsa {
 
 namespace {
 
-constexpr int kOdfThreads = 1024;
+constexpr int kOdfThreads = 512;
+constexpr int kOdfWarps = kOdfThreads / 32;
 constexpr int kMaxSteps = 32;
 constexpr int kMaxTargets = kMaxSteps - 1;
 constexpr int kL1Bins = 2048;
+constexpr int kCand = 6144;                  // candidate buffer (32-bit patterns)
 constexpr unsigned long long kOne = 1ull << 40;
 constexpr unsigned long long kLowMask = kOne - 1;
 
 struct Target {
-    long long k;          // rank (0-based) of the order statistic
-    int slot;             // distinct-prefix slot at the current level
-    unsigned prefix;      // bits resolved so far
-    long long cnt_lt;     // values below the current prefix range
-    unsigned long long iv_lt;   // exact sum (group units) of values of the target's exponent group below it
-    int total;            // 1 when k >= n (S is the total)
+    long long k;                 // rank (0-based) of the order statistic
+    long long cnt_lt;            // values below the current prefix range
+    unsigned long long iv_lt;    // exact sum (group units) of the group's values below the prefix range
+    unsigned prefix;             // bits resolved so far
+    int slot;                    // distinct-prefix slot at the current level
+    int total;                   // 1 when k >= n (S is the total)
 };
 
 __device__ __forceinline__ unsigned long long group_base(unsigned E) { return E >= 1 ? (1ull << 23) : 0ull; }
+
+// Visit every value of x[0..n) once, 16-byte vector loads for the aligned body.
+template <class F>
+__device__ __forceinline__ void for_each_value(const float* __restrict__ x, long long n, F&& f) {
+    const int tid = threadIdx.x;
+    const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
+    long long head = mis ? (long long)(4u - mis) : 0;
+    if (head > n) head = n;
+    if (tid < head) f(__float_as_uint(__ldg(x + tid)));
+    const float4* body = reinterpret_cast<const float4*>(x + head);
+    const long long nv = (n - head) >> 2;
+    for (long long i = tid; i < nv; i += kOdfThreads) {
+        const float4 q = __ldg(body + i);
+        f(__float_as_uint(q.x));
+        f(__float_as_uint(q.y));
+        f(__float_as_uint(q.z));
+        f(__float_as_uint(q.w));
+    }
+    const long long t0 = head + (nv << 2);
+    if (t0 + tid < n) f(__float_as_uint(__ldg(x + t0 + tid)));
+}
+
+// Histogram add aggregated over a warp: neighbouring grid points usually fall into the
+// same bin, and 32 lanes adding to one shared address serialise.  A segmented scan over
+// runs of equal keys (Hillis-Steele with head flags) sums each run, and only the last lane
+// of a run issues the atomic.  key < 0 means "nothing to add".  All 32 lanes must call.
+__device__ __forceinline__ void warp_hist_add(unsigned long long* __restrict__ h, int key, unsigned long long val,
+                                              int lane) {
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    bool flag = lane == 0 || prev != key;
+    const bool tail = lane == 31 || next != key;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, val, d);
+        const bool g = __shfl_up_sync(0xffffffffu, flag, d);
+        if (lane >= d && !flag) val += y;
+        if (lane >= d) flag = flag || g;
+    }
+    if (tail && key >= 0) atomicAdd(&h[key], val);
+}
+
+// One warp resolves one target inside its slot's 2^wb-bin histogram h (packed counts and
+// low-bit sums): finds the sub-bin holding rank t.k and adds the counts and exact sums
+// of all lower sub-bins.
+__device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long* __restrict__ h, int wb, int sh,
+                                             int lane) {
+    const int nb = 1 << wb;
+    const int per = nb >= 32 ? nb / 32 : 1;
+    const unsigned E = t.prefix >> 23;
+    const unsigned long long pbase = group_base(E) + (t.prefix & 0x7fffffu);
+    long long cnt = 0;
+    for (int m = 0; m < per; ++m) {
+        const int b = lane * per + m;
+        if (b < nb) cnt += (long long)(h[b] >> 40);
+    }
+    long long incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const long long before = incl - cnt + t.cnt_lt;
+    const bool mine = cnt > 0 && (t.k >= before) && (t.k < before + cnt);
+    const unsigned owner = __ballot_sync(0xffffffffu, mine);
+    const int ow = owner ? __ffs(owner) - 1 : 31;
+    unsigned long long ivs = 0;
+    long long cnt_below = 0;
+    int found = 0;
+    if (lane < ow) {
+        for (int m = 0; m < per; ++m) {
+            const int b = lane * per + m;
+            if (b < nb) ivs += (h[b] >> 40) * (pbase + ((unsigned long long)b << sh)) + (h[b] & kLowMask);
+        }
+    } else if (lane == ow) {
+        long long run = before;
+        for (int m = 0; m < per; ++m) {
+            const int b = lane * per + m;
+            if (b >= nb) break;
+            const long long c = (long long)(h[b] >> 40);
+            if (t.k < run + c) { found = b; break; }
+            run += c;
+            ivs += (unsigned long long)c * (pbase + ((unsigned long long)b << sh)) + (h[b] & kLowMask);
+        }
+        cnt_below = run;
+    }
+    for (int d = 16; d > 0; d >>= 1) ivs += __shfl_down_sync(0xffffffffu, ivs, d);
+    found = __shfl_sync(0xffffffffu, found, ow);
+    cnt_below = __shfl_sync(0xffffffffu, cnt_below, ow);
+    if (lane == 0) {
+        t.iv_lt += ivs;
+        t.cnt_lt = cnt_below;
+        t.prefix |= (unsigned)found << sh;
+    }
+}
 
 __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ kappa, int64_t N, int K,
                                                      const int64_t* __restrict__ bounds, int n_steps,
                                                      const double* __restrict__ cw, const double* __restrict__ w,
                                                      double* __restrict__ out) {
     extern __shared__ unsigned long long sm[];
-    unsigned long long* h1 = sm;                                  // [2048]
-    unsigned long long* h2 = sm + kL1Bins;                        // [kMaxTargets][256]
-    __shared__ int cbefore[kL1Bins];
+    const int nt = n_steps - 1;
+    const int nslots = nt > 4 ? nt : 4;
+    unsigned long long* h1 = sm;                             // [2048]
+    unsigned long long* h2 = sm + kL1Bins;                   // [nslots][256]; its first 8 KB double as cbefore
+    int* cbefore = reinterpret_cast<int*>(h2);               // [2048] (only before the levels)
+    unsigned* cand = reinterpret_cast<unsigned*>(h2 + (size_t)nslots * 256);   // [kCand]
     __shared__ short slot1[kL1Bins];
     __shared__ unsigned long long gsum[256];
     __shared__ double gpre[257];
     __shared__ Target tg[kMaxTargets];
-    __shared__ unsigned dpre[kMaxTargets];      // distinct prefixes of the current level
-    __shared__ int n_distinct;
+    __shared__ unsigned dpre[kMaxTargets];
+    __shared__ int n_distinct, n_cand;
     __shared__ long long s_zero;
-    __shared__ int wtot[32];
+    __shared__ int wtot[kOdfWarps];
 
     const int k = blockIdx.x, row = blockIdx.y;
     const int64_t b0 = bounds[k], b1 = bounds[k + 1];
     const long long n = b1 - b0;
     const float* x = kappa + (size_t)row * N + b0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nt = n_steps - 1;
 
     for (int i = tid; i < kL1Bins; i += kOdfThreads) { h1[i] = 0ull; slot1[i] = -1; }
-    if (tid == 0) s_zero = 0;
+    if (tid == 0) { s_zero = 0; n_cand = 0; }
     __syncthreads();
 
-    // ---- pass 1: 11-bit histogram with exact low-bit sums
+    // ---- pass 1 (HBM): level-1 histogram with exact low-bit sums
     long long zeros = 0;
-    for (long long i = tid; i < n; i += kOdfThreads) {
-        const unsigned bits = __float_as_uint(__ldg(x + i)) & 0x7fffffffu;
-        if (bits == 0u) { ++zeros; continue; }
-        atomicAdd(&h1[bits >> 20], kOne | (unsigned long long)(bits & 0xfffffu));
+    {
+        auto one = [&](unsigned bits, bool valid) {
+            bits &= 0x7fffffffu;
+            const bool use = valid && bits != 0u;
+            if (valid && bits == 0u) ++zeros;
+            warp_hist_add(h1, use ? (int)(bits >> 20) : -1, kOne | (unsigned long long)(bits & 0xfffffu), lane);
+        };
+        const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
+        long long head = mis ? (long long)(4u - mis) : 0;
+        if (head > n) head = n;
+        const float4* body = reinterpret_cast<const float4*>(x + head);
+        const long long nv = (n - head) >> 2;
+        const long long t0 = head + (nv << 2);
+        // head and tail (< 4 values each) by the first warp
+        if (warp == 0) {
+            one(lane < head ? __float_as_uint(__ldg(x + lane)) : 0u, lane < head);
+            one(t0 + lane < n ? __float_as_uint(__ldg(x + t0 + lane)) : 0u, t0 + lane < n);
+        }
+        // body: whole warps iterate together so that every lane takes part in the scans
+        const long long span = ((nv + kOdfThreads - 1) / kOdfThreads) * kOdfThreads;
+        for (long long i = tid; i < span; i += kOdfThreads) {
+            const bool v = i < nv;
+            float4 q = v ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            one(__float_as_uint(q.x), v);
+            one(__float_as_uint(q.y), v);
+            one(__float_as_uint(q.z), v);
+            one(__float_as_uint(q.w), v);
+        }
     }
     for (int d = 16; d > 0; d >>= 1) zeros += __shfl_down_sync(0xffffffffu, zeros, d);
     if (lane == 0 && zeros) atomicAdd((unsigned long long*)&s_zero, (unsigned long long)zeros);
@@ -86,10 +211,11 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     if (tid == 0) h1[0] += (unsigned long long)s_zero << 40;
     __syncthreads();
 
-    // ---- exclusive scan of level-1 counts (2 bins per thread)
+    // ---- exclusive scan of the level-1 counts (4 bins per thread)
     {
-        const int c0 = (int)(h1[2 * tid] >> 40), c1 = (int)(h1[2 * tid + 1] >> 40);
-        int v = c0 + c1, incl = v;
+        int c[4], v = 0;
+        for (int m = 0; m < 4; ++m) { c[m] = (int)(h1[4 * tid + m] >> 40); v += c[m]; }
+        int incl = v;
         for (int d = 1; d < 32; d <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
@@ -97,33 +223,28 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         if (lane == 31) wtot[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            int t = wtot[lane], ti = t;
+            int t = lane < kOdfWarps ? wtot[lane] : 0, ti = t;
             for (int d = 1; d < 32; d <<= 1) {
                 int y = __shfl_up_sync(0xffffffffu, ti, d);
                 if (lane >= d) ti += y;
             }
-            wtot[lane] = ti - t;
+            if (lane < kOdfWarps) wtot[lane] = ti - t;
         }
         __syncthreads();
-        const int ex = wtot[warp] + incl - v;
-        cbefore[2 * tid] = ex;
-        cbefore[2 * tid + 1] = ex + c0;
+        int ex = wtot[warp] + incl - v;
+        for (int m = 0; m < 4; ++m) { cbefore[4 * tid + m] = ex; ex += c[m]; }
     }
-    // exact per-exponent-group sums in group units
     if (tid < 256) {
         unsigned long long acc = 0;
         for (int m = 0; m < 8; ++m) {
             const unsigned long long h = h1[tid * 8 + m];
-            const unsigned long long base = group_base(tid) + ((unsigned long long)m << 20);
-            acc += (h >> 40) * base + (h & kLowMask);
+            acc += (h >> 40) * (group_base(tid) + ((unsigned long long)m << 20)) + (h & kLowMask);
         }
         gsum[tid] = acc;
     }
-    // targets
     if (tid < nt) {
         Target t;
-        const double u = cw[tid + 1] * (double)n;
-        t.k = (long long)floor(u);
+        t.k = (long long)floor(cw[tid + 1] * (double)n);
         t.total = t.k >= n;
         t.slot = -1;
         t.prefix = 0;
@@ -133,36 +254,35 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     }
     __syncthreads();
     if (warp == 0) {
-        // FP64 exclusive prefix over the 256 exponent groups
-        double loc[8], run = 0.0;
+        // FP64 exclusive prefix over the 256 exponent groups (the only FP64 reduction)
+        double loc[8];
+        double tot = 0.0;
         for (int m = 0; m < 8; ++m) {
             const int E = lane * 8 + m;
             loc[m] = (double)gsum[E] * ldexp(1.0, (E >= 1 ? E : 1) - 150);
+            tot += loc[m];
         }
-        double tot = 0.0;
-        for (int m = 0; m < 8; ++m) tot += loc[m];
         double incl = tot;
         for (int d = 1; d < 32; d <<= 1) {
             double y = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += y;
         }
-        run = incl - tot;
+        double run = incl - tot;
         for (int m = 0; m < 8; ++m) {
             gpre[lane * 8 + m] = run;
             run += loc[m];
         }
         if (lane == 31) gpre[256] = run;
     }
-    // locate each target's level-1 bin
+    // each target's level-1 bin (the thread owning that bin records it)
     for (int t = 0; t < nt; ++t) {
         if (tg[t].total) continue;
         const long long kk = tg[t].k;
-        for (int bb = 2 * tid; bb < 2 * tid + 2; ++bb) {
+        for (int bb = 4 * tid; bb < 4 * tid + 4; ++bb) {
             const long long c = (long long)(h1[bb] >> 40);
             if (c > 0 && cbefore[bb] <= kk && kk < cbefore[bb] + c) {
                 tg[t].prefix = (unsigned)bb << 20;
                 tg[t].cnt_lt = cbefore[bb];
-                // exact sum of the bins of the same exponent group below bb
                 unsigned long long acc = 0;
                 for (int m = bb & ~7; m < bb; ++m) {
                     const unsigned long long h = h1[m];
@@ -173,15 +293,44 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         }
     }
     __syncthreads();
+    if (tid == 0) {
+        int nd = 0;
+        for (int t = 0; t < nt; ++t) {
+            if (tg[t].total) continue;
+            const int b = (int)(tg[t].prefix >> 20);
+            if (slot1[b] < 0) slot1[b] = (short)nd++;
+        }
+        n_distinct = nd;
+    }
+    __syncthreads();
 
-    // ---- levels 2..4
+    // ---- pass 2 (L2): candidates = non-zero values in a target's level-1 bin
+    if (n_distinct > 0) {
+        for_each_value(x, n, [&](unsigned bits) {
+            bits &= 0x7fffffffu;
+            const bool c = bits != 0u && slot1[bits >> 20] >= 0;
+            const unsigned act = __activemask();
+            const unsigned bal = __ballot_sync(act, c);
+            if (!c) return;
+            const int leader = __ffs(bal) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&n_cand, __popc(bal));
+            base = __shfl_sync(bal, base, leader);
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (pos < kCand) cand[pos] = bits;
+        });
+    }
+    __syncthreads();
+    const int nc = n_cand;
+    const bool in_smem = nc <= kCand;
+
+    // ---- levels 2..4 on the candidates (or on the interval again if they overflowed)
     const int shifts[3] = {12, 4, 0};
     const int widths[3] = {8, 8, 4};
     for (int lvl = 0; lvl < 3; ++lvl) {
         const int sh = shifts[lvl], wb = widths[lvl];
-        const int hiShift = sh + wb;      // bits at and above hiShift are the resolved prefix
+        const int hiShift = sh + wb;
         const int nbins = 1 << wb;
-        // distinct prefixes of the active targets
         if (tid == 0) {
             int nd = 0;
             for (int t = 0; t < nt; ++t) {
@@ -197,48 +346,34 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         __syncthreads();
         const int nd = n_distinct;
         for (int i = tid; i < nd * 256; i += kOdfThreads) h2[i] = 0ull;
-        if (lvl == 0)
-            for (int q = tid; q < nd; q += kOdfThreads) slot1[dpre[q] >> 20] = (short)q;
         __syncthreads();
-        if (nd > 0) {
-            for (long long i = tid; i < n; i += kOdfThreads) {
-                const unsigned bits = __float_as_uint(__ldg(x + i)) & 0x7fffffffu;
-                if (bits == 0u || slot1[bits >> 20] < 0) continue;
-                const unsigned pre = (bits >> hiShift) << hiShift;
-                int q = -1;
-                if (lvl == 0) q = slot1[bits >> 20];
-                else
-                    for (int r = 0; r < nd; ++r)
-                        if (dpre[r] == pre) q = r;
-                if (q < 0) continue;
-                const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
-                const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
-                atomicAdd(&h2[q * 256 + sub], kOne | low);
-            }
+        auto add = [&](unsigned bits) {
+            const unsigned pre = (bits >> hiShift) << hiShift;
+            int q = -1;
+            for (int r = 0; r < nd; ++r)
+                if (dpre[r] == pre) q = r;
+            if (q < 0) return;
+            const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
+            const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
+            atomicAdd(&h2[q * 256 + sub], kOne | low);
+        };
+        if (in_smem) {
+            for (int i = tid; i < nc; i += kOdfThreads) add(cand[i]);
+        } else {
+            for_each_value(x, n, [&](unsigned bits) {
+                bits &= 0x7fffffffu;
+                if (bits == 0u || slot1[bits >> 20] < 0) return;
+                add(bits);
+            });
         }
         __syncthreads();
-        // zeros belong to the all-zero prefix
         if (tid < nd && dpre[tid] == 0u) h2[tid * 256] += (unsigned long long)s_zero << 40;
         __syncthreads();
-        // resolve each target inside its slot (one thread per target; <= 256 bins)
-        if (tid < nt && !tg[tid].total) {
-            Target t = tg[tid];
-            const unsigned long long* h = h2 + t.slot * 256;
-            long long before = t.cnt_lt;
-            const unsigned E = t.prefix >> 23;
-            // integer value of the prefix (without the low bits) in group units
-            const unsigned long long pbase = group_base(E) + (t.prefix & 0x7fffffu);
-            for (int bb = 0; bb < nbins; ++bb) {
-                const long long c = (long long)(h[bb] >> 40);
-                if (t.k < before + c) {
-                    t.prefix |= (unsigned)bb << sh;
-                    break;
-                }
-                before += c;
-                t.iv_lt += (unsigned long long)c * (pbase + ((unsigned long long)bb << sh)) + (h[bb] & kLowMask);
-            }
-            t.cnt_lt = before;
-            tg[tid] = t;
+        for (int t = warp; t < nt; t += kOdfWarps) {
+            if (tg[t].total) continue;
+            Target tt = tg[t];
+            resolve_warp(tt, h2 + tt.slot * 256, wb, sh, lane);
+            if (lane == 0) tg[t] = tt;
         }
         __syncthreads();
     }
@@ -246,7 +381,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     // ---- step means
     if (tid < n_steps) {
         const int s = tid;
-        auto S = [&](int bidx) -> double {   // S(c_bidx * n)
+        auto S = [&](int bidx) -> double {
             if (bidx == 0) return 0.0;
             if (bidx == n_steps) return gpre[256];
             const Target& t = tg[bidx - 1];
@@ -256,11 +391,16 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             const double theta = (double)__uint_as_float(t.prefix);
             const double below = gpre[E] + (double)t.iv_lt * unit;
             const double u = cw[bidx] * (double)n;
-            return below + (double)(t.k - t.cnt_lt) * theta + (u - (double)t.k) * theta;
+            return below + (u - (double)t.cnt_lt) * theta;
         };
-        const double m = (S(s + 1) - S(s)) / (w[s] * (double)n);
-        out[((size_t)row * K + k) * n_steps + s] = m;
+        out[((size_t)row * K + k) * n_steps + s] = (S(s + 1) - S(s)) / (w[s] * (double)n);
     }
+}
+
+size_t odf_smem_bytes(int n_steps) {
+    const int nt = n_steps - 1;
+    const int nslots = nt > 4 ? nt : 4;
+    return (kL1Bins + (size_t)nslots * 256) * sizeof(unsigned long long) + kCand * sizeof(unsigned);
 }
 
 }  // namespace
@@ -283,7 +423,7 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
         if (len < 1) return fail(MPSA_EINVAL, "build_odf: bounds not strictly increasing at %d", k);
         if (len >= (1 << 21)) return fail(MPSA_EINVAL, "build_odf: interval %d has %lld points (max 2^21-1)", k, (long long)len);
     }
-    // cumulative widths: FP64 left-to-right partial sums, last forced to 1
+    // cumulative widths: FP64 left-to-right partial sums, the last forced to 1
     std::vector<double> cw(n_steps + 1);
     double acc = 0.0;
     cw[0] = 0.0;
@@ -304,11 +444,11 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_b, bounds, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_cw, cw.data(), (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_w, widths, n_steps * sizeof(double), cudaMemcpyHostToDevice, st));
-    const size_t smem = (kL1Bins + (size_t)(n_steps - 1 > 0 ? n_steps - 1 : 1) * 256) * sizeof(unsigned long long);
+    const size_t smem = odf_smem_bytes(n_steps);
     static unsigned attr_set = 0;   // one bit per device
     if (!(attr_set & (1u << (ctx->device & 31)))) {
         MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((kL1Bins + kMaxTargets * 256) * sizeof(unsigned long long))));
+                                           (int)odf_smem_bytes(kMaxSteps)));
         attr_set |= 1u << (ctx->device & 31);
     }
     prof_mark(ctx, MPSA_KERNEL_ODF, st);

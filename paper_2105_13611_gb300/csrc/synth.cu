@@ -427,18 +427,20 @@ struct TileArgs {
 
 struct NearRec {
     float cf, f, klnq, a, srel, kv;
-    int flags;       // klo | khi << 3 | check << 6 | series << 7
-    int pad;
+    int flags;       // klo | khi << 3 | check << 6 | series << 7 | full << 8
+    int jlo, jhi;    // outer cut window (grid indices)
+    int pad[3];
 };
 
 // far line: v = G_k * kvB + kvE1 (exact expm1 decomposition around the tile start),
 // H by the far tier with the 1/(1 + 8 a^2 y^2) factor only when a^2 is not negligible.
-template <bool EPS, bool CHK>
-__device__ __forceinline__ void far_line(const float4 p, float A8, int klo, int khi, const float (&G)[8],
+// The 8 points are evaluated without branches so that their dependency chains
+// interleave; MASKED lines (partial coverage or points near the cut) select with a mask.
+template <bool EPS, bool MASKED>
+__device__ __forceinline__ void far_line(const float4 p, float A8, int klo, int khi, bool chk, const float (&G)[8],
                                          float (&part)[8]) {
 #pragma unroll
     for (int k = 0; k < kPtsPerThread; ++k) {
-        if (k < klo || k > khi) continue;
         const float v = fmaf(G[k], p.x, p.y);
         const float y = rcp_approx(fmaf(2.f * v, v, p.z));
         float l = p.w * y * fmaf(4.f, y, 2.f);
@@ -446,29 +448,42 @@ __device__ __forceinline__ void far_line(const float4 p, float A8, int klo, int 
             const float e = A8 * y * y;
             l *= fmaf(e, e - 1.f, 1.f);
         }
-        if (CHK) l = (l >= 1.f) ? l : 0.f;
+        if (MASKED) {
+            bool ok = (k >= klo) & (k <= khi);
+            if (chk) ok = ok & (l >= 1.f);
+            l = ok ? l : 0.f;
+        }
         part[k] += l;
     }
 }
 
-template <bool CHK>
-__device__ __forceinline__ void near_line(const NearRec& r, int klo, int khi, bool series, const float (&jf)[8],
+// near line: exact offset d = (j - c) - f and the expm1 series for v; the tiers of H
+// branch per point.  Lines that do not cover the whole tile are culled per warp in
+// 32-point segments (a warp's lanes own 32 consecutive points of each slot).
+template <bool FULL, bool CHK>
+__device__ __forceinline__ void near_line(const NearRec& r, int seg0, bool series, const float (&jf)[8],
                                           float q1, float q2, float q3, float lnq, float (&part)[8]) {
 #pragma unroll
     for (int k = 0; k < kPtsPerThread; ++k) {
-        if (k < klo || k > khi) continue;
+        if (!FULL) {
+            const int lo = seg0 + k * kTileThreads;
+            if (lo + 31 < r.jlo || lo > r.jhi) continue;
+        }
         const float d = (jf[k] - r.cf) - r.f;
         float v;
         if (series) v = r.klnq * (d * fmaf(d, fmaf(d, fmaf(d, q3, q2), q1), 1.f));
         else v = r.kv * expm1f(-d * lnq);
-        float l = r.srel * voigt_H(v, r.a);
+        float l = r.srel * voigt_H_lean(v, r.a);
         if (CHK) l = (l >= 1.f) ? l : 0.f;
         part[k] += l;
     }
 }
 
+#ifndef MPSA_TILES_MINB
+#define MPSA_TILES_MINB 3
+#endif
 template <int PREC>
-__global__ void __launch_bounds__(kTileThreads) k_tiles(TileArgs g) {
+__global__ void __launch_bounds__(kTileThreads, MPSA_TILES_MINB) k_tiles(TileArgs g) {
     __shared__ float4 sFarA[kTileThreads];
     __shared__ float2 sFarB[kTileThreads];
     __shared__ NearRec sNear[kTileThreads];
@@ -515,16 +530,18 @@ __global__ void __launch_bounds__(kTileThreads) k_tiles(TileArgs g) {
                     const int klo = max(0, (jlo - J0) >> 8), khi = min(kPtsPerThread - 1, (jhi - J0) >> 8);
                     const int P0 = J0 + klo * kTileThreads, P1 = J0 + khi * kTileThreads + kTileThreads - 1;
                     const bool check = !(g.ilo[q] <= P0 && g.ihi[q] >= P1);
-                    // distance from the centre x0 = c + f to the nearest evaluated point
+                    // distance from the centre x0 = c + f to the nearest point of the tile
+                    // (far lines are evaluated at all 8 points, masked to [klo, khi])
+                    const int T0 = J0, T1 = J0 + kTile - 1;
                     float dist;
                     bool red;
-                    if (c + 1 <= P0) { dist = (float)(P0 - c) - f; red = true; }
-                    else if (c >= P1) { dist = f + (float)(c - P1); red = false; }
+                    if (c + 1 <= T0) { dist = (float)(T0 - c) - f; red = true; }
+                    else if (c >= T1) { dist = f + (float)(c - T1); red = false; }
                     else { dist = 0.f; red = true; }
                     float vmin = 0.f;
                     if (dist >= (float)kFarDist)
                         vmin = red ? -kv * expm1f(-dist * g.lnq) : kv * expm1f(dist * g.lnq);
-                    const int flags = klo | (khi << 3) | (check ? 64 : 0);
+                    const int flags = klo | (khi << 3) | (check ? 64 : 0) | ((klo == 0 && khi == kPtsPerThread - 1) ? 256 : 0);
                     if (dist >= (float)kFarDist && vmin >= kFarV) {
                         isFar = true;
                         const float D = (float)(J0 - c) - f;
@@ -545,7 +562,9 @@ __global__ void __launch_bounds__(kTileThreads) k_tiles(TileArgs g) {
                         nr.srel = srel;
                         nr.kv = kv;
                         nr.flags = flags | (series ? 128 : 0);
-                        nr.pad = 0;
+                        nr.jlo = jlo;
+                        nr.jhi = jhi;
+                        nr.pad[0] = nr.pad[1] = nr.pad[2] = 0;
                     }
                 }
             }
@@ -579,20 +598,27 @@ __global__ void __launch_bounds__(kTileThreads) k_tiles(TileArgs g) {
                 const int fl = __float_as_int(q.y);
                 const int klo = fl & 7, khi = (fl >> 3) & 7;
                 const bool chk = fl & 64, eps = fl & 128;
+                const bool plain = (fl & 256) && !chk;     // all 8 points, no cut test
                 if (eps) {
-                    if (chk) far_line<true, true>(p, q.x, klo, khi, G, part);
-                    else far_line<true, false>(p, q.x, klo, khi, G, part);
+                    if (plain) far_line<true, false>(p, q.x, klo, khi, chk, G, part);
+                    else far_line<true, true>(p, q.x, klo, khi, chk, G, part);
                 } else {
-                    if (chk) far_line<false, true>(p, q.x, klo, khi, G, part);
-                    else far_line<false, false>(p, q.x, klo, khi, G, part);
+                    if (plain) far_line<false, false>(p, q.x, klo, khi, chk, G, part);
+                    else far_line<false, true>(p, q.x, klo, khi, chk, G, part);
                 }
             }
+            const int seg0 = J0 + warp * 32;
             for (int r = 0; r < nNear; ++r) {
                 const NearRec nrr = sNear[r];
-                const int klo = nrr.flags & 7, khi = (nrr.flags >> 3) & 7;
                 const bool series = nrr.flags & 128;
-                if (nrr.flags & 64) near_line<true>(nrr, klo, khi, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
-                else near_line<false>(nrr, klo, khi, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                const bool full = nrr.flags & 256, chk = nrr.flags & 64;
+                if (full) {
+                    if (chk) near_line<true, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                    else near_line<true, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                } else {
+                    if (chk) near_line<false, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                    else near_line<false, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                }
             }
             if (PREC == MPSA_PREC_FP32_COMPENSATED) {
                 // fold the chunk's FP32 partial sums into the Kahan-compensated totals

@@ -125,4 +125,16 @@ __device__ __forceinline__ float voigt_H(float v, float a) {
     return voigt_core(v, a);
 }
 
+// The same function with the two inner tiers as out-of-line calls: used where it is
+// replicated many times in one kernel (the far tier, taken by most points, stays inline).
+static __device__ __noinline__ float voigt_inner_tiers(float v, float a) {
+    return (v * v + a * a >= 36.f) ? voigt_mid(v, a) : voigt_core(v, a);
+}
+__device__ __forceinline__ float voigt_H_lean(float v, float a) {
+    v = fabsf(v);
+    const float V = v * v, A = a * a;
+    if (V + A >= 1600.f) return voigt_far(V, A, a * kInvSqrtPi);
+    return voigt_inner_tiers(v, a);
+}
+
 }  // namespace mpsa
