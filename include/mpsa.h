@@ -180,6 +180,27 @@ int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N,
               int32_t K, const int64_t* bounds, int32_t n_steps, const double* widths,
               int32_t mean_kind, double* odf_out, void* stream);
 
+/*
+ * build_odf_noalloc -- build_odf that allocates no device memory.  The paper has
+ * no counterpart: this is an operational variant for callers that must not
+ * allocate, e.g. a process whose device memory belongs to another framework's
+ * caching allocator, or a latency-critical loop in which cudaMalloc (or a
+ * cudaFree that may synchronise the device) is not allowed.
+ *   device: CUDA device to run on (made current by the call).
+ *   The other arguments, results and errors are those of build_odf (no context
+ *   is needed); K must not exceed 65536 intervals (MPSA_EINVAL otherwise).
+ * The interval bounds and widths are staged in one fixed file-scope device array
+ * of about 0.5 MiB, which every device that loads the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make this first call before any stream
+ * capture.  Every call shares the array and overwrites it: calls that may
+ * overlap on the GPU (different streams, or a capture replayed concurrently)
+ * race and must be serialised by the caller.  Stream-ordered otherwise.
+ */
+int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_rows, int64_t N,
+                      int32_t K, const int64_t* bounds, int32_t n_steps, const double* widths,
+                      int32_t mean_kind, double* odf_out, void* stream);
+
 /* One model atmosphere for synth_spectrum (host arrays of length n_depth,
  * ordered from the top down): column mass m [g cm^-2], T [K], P [dyn cm^-2]. */
 typedef struct {

@@ -20,7 +20,7 @@ MEAN_ARITH, MEAN_GEOM = 0, 1
 
 EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "mpsa_grid_size",
             "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
-            "mpsa_profile_enable", "mpsa_profile_read"]
+            "mpsa_profile_enable", "mpsa_profile_read", "build_odf_noalloc"]
 KERNEL_PROFILE, KERNEL_ODF = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -82,6 +82,9 @@ def load_library(path: str = LIB_PATH):
                               C.c_int32, vp, vp]
     lib.synth_spectrum.argtypes = [vp, C.POINTER(Atmos), C.POINTER(LGrid), C.c_int32, _dp, vp,
                                    C.POINTER(SynthOpts), vp]
+    lib.build_odf_noalloc.argtypes = [C.c_int32, vp, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.c_int32,
+                                      _dp, C.c_int32, vp, vp]
+    lib.build_odf_noalloc.restype = C.c_int
     lib.mpsa_profile_enable.argtypes = [vp, C.c_int]
     lib.mpsa_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     for f in ("mpsa_create", "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
@@ -129,6 +132,17 @@ def grid_size(lam0_nm, lam1_nm, R) -> int:
 
 def make_opts(cut=1e-3, kc_factor=1e-2, precision=PREC_FP32_COMPENSATED):
     return SynthOpts(cut, kc_factor, precision, 0)
+
+
+def build_odf_noalloc(device, kappa, bounds, widths, odf_out, mean_kind=MEAN_ARITH, stream=None):
+    """build_odf without device allocation (fixed library-owned staging array; see include/mpsa.h)."""
+    lib = load_library()
+    b = _arr(bounds, np.int64)
+    w = _arr(widths, np.float64)
+    n_rows, N = kappa.shape
+    rc = lib.build_odf_noalloc(int(device), _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
+                               _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream))
+    _check(rc)
 
 
 class Context:

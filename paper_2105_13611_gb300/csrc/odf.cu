@@ -457,3 +457,93 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// build_odf_noalloc: build_odf without any device allocation.
+//
+// build_odf stages the interval bounds and the sub-bin widths in stream-ordered
+// scratch (cudaMallocAsync).  This entry point stages them instead in the fixed
+// file-scope array below, for callers that must not allocate device memory: a
+// process whose device memory is entirely owned by another framework's caching
+// allocator, or a latency-critical loop where an allocation (or a cudaFree that
+// may synchronise the device) is not allowed.  The array is resident on every
+// device that loads the library, until the process exits.
+namespace mpsa {
+namespace {
+
+constexpr int kNoAllocMaxIntervals = 65536;
+constexpr size_t kNoAllocBytes =
+    (size_t)(kNoAllocMaxIntervals + 1) * sizeof(int64_t) + (size_t)(2 * kMaxSteps + 1) * sizeof(double);
+static __device__ __align__(256) unsigned char g_odf_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the scratch array, per device.  In host code the symbol name is
+// only a host-side stand-in; the address comes from cudaGetSymbolAddress with the
+// device current.
+static void* g_noalloc_ptr[64];
+
+int noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= 64) return fail(MPSA_EINVAL, "build_odf_noalloc: device %d", device);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_odf_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MPSA_ECUDA, "build_odf_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
+    return MPSA_OK;
+}
+
+}  // namespace
+}  // namespace mpsa
+
+extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_rows, int64_t N, int32_t K,
+                                 const int64_t* bounds, int32_t n_steps, const double* widths, int32_t mean_kind,
+                                 double* odf_out, void* stream) {
+    if (!kappa || !bounds || !widths || !odf_out) return fail(MPSA_EINVAL, "build_odf_noalloc: NULL argument");
+    if (K > kNoAllocMaxIntervals)
+        return fail(MPSA_EINVAL, "build_odf_noalloc: K = %d intervals exceeds the fixed scratch limit of %d", K,
+                    kNoAllocMaxIntervals);
+    if (n_rows < 1 || N < 1 || K < 1)
+        return fail(MPSA_EINVAL, "build_odf_noalloc: n_rows %d N %lld K %d", n_rows, (long long)N, K);
+    if (n_steps < 1 || n_steps > kMaxSteps)
+        return fail(MPSA_EINVAL, "build_odf_noalloc: n_steps = %d (1..%d)", n_steps, kMaxSteps);
+    if (mean_kind != MPSA_MEAN_ARITH)
+        return fail(MPSA_EINVAL, "build_odf_noalloc: mean_kind %d not available (arithmetic only)", mean_kind);
+    if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds outside [0, N]");
+    for (int k = 0; k < K; ++k) {
+        const int64_t len = bounds[k + 1] - bounds[k];
+        if (len < 1) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds not strictly increasing at %d", k);
+        if (len >= (1 << 21))
+            return fail(MPSA_EINVAL, "build_odf_noalloc: interval %d has %lld points (max 2^21-1)", k, (long long)len);
+    }
+    double cw[kMaxSteps + 1];
+    double acc = 0.0;
+    cw[0] = 0.0;
+    for (int s = 0; s < n_steps; ++s) {
+        if (!(widths[s] > 0) || !isfinite(widths[s]))
+            return fail(MPSA_EINVAL, "build_odf_noalloc: widths[%d] = %g", s, widths[s]);
+        acc = acc + widths[s];
+        cw[s + 1] = acc;
+    }
+    if (fabs(acc - 1.0) > 1e-12) return fail(MPSA_EINVAL, "build_odf_noalloc: widths sum to %.17g", acc);
+    cw[n_steps] = 1.0;
+    MPSA_CUDA_TRY(cudaSetDevice(device));
+    unsigned char* base;
+    int r;
+    if ((r = noalloc_scratch(device, &base))) return r;
+    // layout: bounds [K+1] int64 | cumulative widths [n_steps+1] | widths [n_steps]
+    int64_t* d_b = reinterpret_cast<int64_t*>(base);
+    double* d_cw = reinterpret_cast<double*>(base + (size_t)(kNoAllocMaxIntervals + 1) * sizeof(int64_t));
+    double* d_w = d_cw + (kMaxSteps + 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    MPSA_CUDA_TRY(cudaMemcpyAsync(d_b, bounds, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(d_cw, cw, (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(d_w, widths, n_steps * sizeof(double), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)odf_smem_bytes(kMaxSteps)));
+    k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_b, n_steps, d_cw, d_w,
+                                                                         odf_out);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
