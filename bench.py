@@ -52,6 +52,11 @@ def parse():
     p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank (table workload)")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
+    p.add_argument("--mode", choices=["step", "serve"], default="step",
+                   help="step: the throughput benchmark; serve: Poisson request stream through the server")
+    p.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of the request stream")
+    p.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
+    p.add_argument("--serve-limit", type=float, default=90.0, help="wall-clock limit of a serving run [s]")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -365,8 +370,115 @@ def native_arm(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
+    """Poisson arrivals of mixed requests (the serving workload).
+
+    Spectrum: grey atmosphere with D ~ U{40..120} depths, Teff ~ U(3500, 12000) K, log g ~ U(1, 5);
+    window length ~ logU(1, 500) nm placed uniformly in 9-10000 nm at R = 5e5; 5 mu angles.
+    ODF: one composition x the 57 x 25 T-P grid over 1-10 contiguous intervals of the 328-interval grid."""
+    from oracle import spectrum as spc  # grey-law atmosphere builder only (no synthesis)
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        if rng.random() < spectrum_fraction:
+            D = int(rng.integers(40, 121))
+            Teff, logg = rng.uniform(3500, 12000), rng.uniform(1, 5)
+            L = float(np.exp(rng.uniform(math.log(1.0), math.log(500.0))))
+            lam0 = float(rng.uniform(9.0, 10000.0 - L))
+            m, T, P = spc.grey_atmosphere(D, Teff, logg)
+            out.append((t, "spectrum", (m, T, P, wl.Grid(lam0, lam0 + L, 5e5))))
+        else:
+            nint = int(rng.integers(1, 11))
+            k0 = int(rng.integers(0, 328 - nint + 1))
+            out.append((t, "odf", (k0, nint)))
+    return out
+
+
+def serve_arm(args):
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    bounds_full = wl.equal_intervals(N, w.n_intervals)
+    lnq = math.log1p(1.0 / w.grid.R)
+    mus = [1.0, 0.8, 0.6, 0.4, 0.2]
+    rows = np.arange(len(w.T), dtype=np.int32)
+
+    def odf_args(k0, nint):
+        j0, j1 = int(bounds_full[k0]), int(bounds_full[k0 + nint])
+        lam_a = w.grid.lam0_nm * math.exp(j0 * lnq)
+        g = wl.Grid(lam_a, lam_a * math.exp((j1 - j0 - 1) * lnq) * (1 + 1e-12), w.grid.R)
+        n_sub = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
+        b = np.minimum(bounds_full[k0:k0 + nint + 1] - j0, n_sub)
+        return rows, g, b, w.widths
+
+    def run_stream(stream, max_inflight, limit):
+        ctx = binding.Context(0)
+        ctx.load_linelist(lines, se, ss)
+        ctx.set_atmosphere_grid(el, w.T, w.P)
+        srv = binding.Server(ctx, hbm_budget_bytes=int(120e9), max_inflight=max_inflight, rows_per_chunk=8)
+        t0 = time.perf_counter()
+        pending = []
+        i = 0
+        lat = {"spectrum": [], "odf": []}
+        while time.perf_counter() - t0 < limit:
+            now = time.perf_counter() - t0
+            while i < len(stream) and stream[i][0] <= now:
+                _, kind, a = stream[i]
+                tk = srv.submit_spectrum(*a[:3], a[3], mus) if kind == "spectrum" else srv.submit_odf(*odf_args(*a))
+                pending.append((tk, kind))
+                i += 1
+            still = []
+            for tk, kind in pending:
+                try:
+                    _, ms = srv.wait(tk, timeout_ms=0)
+                    lat[kind].append(ms)
+                except binding.MpsaError as e:
+                    if e.code == binding.MPSA_ETIMEOUT:
+                        still.append((tk, kind))
+                    else:
+                        raise
+            pending = still
+            if i >= len(stream) and not pending:
+                break
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        n_cancel = srv.cancel_queued()
+        srv.close()
+        ctx.close()
+        done = sum(len(v) for v in lat.values())
+        allv = sorted(lat["spectrum"] + lat["odf"])
+        pct = lambda v, q: float(np.percentile(v, q)) if v else None
+        return {"offered": len(stream), "submitted": i, "completed": done, "cancelled_unadmitted": n_cancel,
+                "wall_s": wall, "throughput_req_s": done / wall,
+                "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
+                "spectrum": {"n": len(lat["spectrum"]), "p50_ms": pct(lat["spectrum"], 50), "p99_ms": pct(lat["spectrum"], 99)},
+                "odf": {"n": len(lat["odf"]), "p50_ms": pct(lat["odf"], 50), "p99_ms": pct(lat["odf"], 99)}}
+
+    stream = make_request_stream(args.serve_rate, args.serve_seconds, seed=2024)
+    res = run_stream(stream, 8, args.serve_limit)
+    # the same requests one at a time (no overlap), as many as fit in the same wall-clock limit
+    seq = run_stream(stream, 1, args.serve_limit)
+    out = {"mode": "serve", "metric": "requests/s and latency", "offered_rate_req_s": args.serve_rate,
+           "arrival_window_s": args.serve_seconds, "mix": "90% spectrum (R=5e5 windows) / 10% ODF (57x25 grid)",
+           "continuous_batching": res, "one_at_a_time": seq,
+           "saturated": res["completed"] < res["offered"], "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "serve":
+        serve_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

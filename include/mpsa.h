@@ -231,6 +231,111 @@ int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_lgrid* win,
                    const mpsa_synth_opts* opts, void* stream);
 
 /*
+ * Batched form: many rows on several grids in one persistent, graph-captured
+ * launch (the paper's method, Eq. l_nu_line + App. E, over a heterogeneous set of
+ * (composition, T, P) rows and wavelength windows).  At creation every group's line
+ * preparation runs once, an autotuner (autotune != 0) times the persistent profile
+ * kernel for each candidate configuration (points per thread, threads per CTA,
+ * CTAs per SM) on a sample of tiles and keeps the fastest per grid point, the
+ * (row, tile) units are ordered by decreasing estimated cost, and the whole
+ * pipeline (preparation of every group, one persistent profile launch, the ODFs)
+ * is captured into a CUDA graph.  mpsa_batch_run replays it on `stream`; the
+ * results equal those of synth_opacity / build_odf within the stated tolerances.
+ * The graph binds the context's resident buffers and the groups' output buffers:
+ * re-create the batch after load_linelist or set_atmosphere_grid.
+ */
+typedef struct {
+    mpsa_lgrid grid;
+    int32_t n_sel;
+    const int32_t* sel;        /* host: population-table rows */
+    float* kappa_out;          /* device float[n_sel][N] */
+    float* kappa_c_out;        /* device float[n_sel] or NULL */
+    int64_t* evals_out;        /* device int64[n_sel] or NULL */
+    int32_t K;                 /* intervals of the ODF of this group; 0 = no ODF */
+    const int64_t* bounds;     /* host int64[K+1] */
+    int32_t n_steps;
+    const double* widths;      /* host */
+    double* odf_out;           /* device double[n_sel][K][n_steps] */
+} mpsa_batch_group;
+
+typedef struct {
+    int32_t pts_per_thread, threads, min_blocks;   /* chosen profile-kernel configuration */
+    int32_t n_rows;
+    int64_t n_units;                                /* (row, tile) work units */
+    int32_t n_tuned;                                /* configurations timed by the autotuner */
+    double tune_ms_per_mpoint[8];                   /* their time per 1e6 grid points */
+} mpsa_batch_info;
+
+typedef struct mpsa_batch mpsa_batch;
+int mpsa_batch_create(mpsa_ctx* ctx, int32_t n_groups, const mpsa_batch_group* groups,
+                      const mpsa_synth_opts* opts, int32_t autotune, void* stream, mpsa_batch** out);
+int mpsa_batch_run(mpsa_batch* b, void* stream);
+int mpsa_batch_get_info(const mpsa_batch* b, mpsa_batch_info* out);
+void mpsa_batch_destroy(mpsa_batch* b);
+
+/*
+ * Request server (continuous batching).  Not a step of the paper's method: the
+ * serving form of the library.  A worker thread owns the context while the
+ * server exists (do not call other entry points on that context meanwhile).
+ * Requests wait in FIFO order; the oldest is started as soon as one of
+ * max_inflight stream slots is free and its estimated device memory fits the
+ * budget, so requests arriving while others run are admitted without waiting
+ * for them and their kernels overlap on the device.  Each request runs exactly
+ * the kernels of the direct entry points (synthesis in chunks of
+ * rows_per_chunk rows to bound scratch), so its result does not depend on what
+ * else is in flight.
+ */
+typedef struct mpsa_server mpsa_server;
+
+#define MPSA_REQ_SPECTRUM 1
+#define MPSA_REQ_ODF      2
+
+typedef struct {
+    int32_t kind;              /* MPSA_REQ_SPECTRUM or MPSA_REQ_ODF */
+    /* spectrum (synth_spectrum's arguments; host arrays copied at submit) */
+    mpsa_atmos atm;
+    mpsa_lgrid win;
+    int32_t n_mu;
+    const double* mu;
+    float* I_out;              /* host float[n_mu][N_win], written on completion */
+    /* ODF: rows of the atmosphere grid, synthesised on `grid` and reduced with
+       build_odf's rules (arithmetic means); host arrays copied at submit */
+    int32_t n_sel;
+    const int32_t* sel;
+    mpsa_lgrid grid;
+    int32_t K;
+    const int64_t* bounds;
+    int32_t n_steps;
+    const double* widths;
+    double* odf_out;           /* host double[n_sel][K][n_steps], written on completion */
+    float* kappa_c_out;        /* host float[n_sel] or NULL */
+} mpsa_request;
+
+typedef struct {
+    int64_t submitted, completed, failed, running, queued;
+    size_t bytes_in_use, bytes_peak;    /* admitted memory estimates */
+} mpsa_server_stats;
+
+/* Create a server on ctx (which needs a line list and an atmosphere grid).
+ * hbm_budget_bytes bounds the summed memory estimates of running requests.
+ * Errors: MPSA_EINVAL, MPSA_ESTATE, MPSA_ECUDA. */
+int mpsa_server_create(mpsa_server** out, mpsa_ctx* ctx, size_t hbm_budget_bytes,
+                       int32_t max_inflight, int32_t rows_per_chunk);
+/* Queue a request; *ticket identifies it.  Output buffers must stay valid until
+ * mpsa_server_wait returns for it.  MPSA_ENOMEM if it alone exceeds the budget. */
+int mpsa_server_submit(mpsa_server* s, const mpsa_request* req, int64_t* ticket);
+/* Wait up to timeout_ms for a request; MPSA_OK when its outputs are written
+ * (latency_ms = completion - submission), MPSA_ETIMEOUT if it is not done yet
+ * (wait again), or the request's error.  A finished ticket is released. */
+int mpsa_server_wait(mpsa_server* s, int64_t ticket, int32_t timeout_ms, double* latency_ms);
+int mpsa_server_get_stats(mpsa_server* s, mpsa_server_stats* out);
+/* Drop every request still waiting for admission (their waits return
+ * MPSA_ESTATE); running requests are not affected. */
+int mpsa_server_cancel_queued(mpsa_server* s, int64_t* n_cancelled);
+/* Finish queued and running requests, then free the server. */
+void mpsa_server_destroy(mpsa_server* s);
+
+/*
  * Kernel timing for measurement tools (not part of the method).  While enabled,
  * the library records a CUDA event pair on the launching stream around each
  * launch of its two dominant kernels: MPSA_KERNEL_PROFILE (the profile kernel

@@ -20,7 +20,11 @@ MEAN_ARITH, MEAN_GEOM = 0, 1
 
 EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "mpsa_grid_size",
             "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
-            "mpsa_profile_enable", "mpsa_profile_read", "build_odf_noalloc"]
+            "mpsa_profile_enable", "mpsa_profile_read", "build_odf_noalloc",
+            "mpsa_server_create", "mpsa_server_submit", "mpsa_server_wait", "mpsa_server_get_stats",
+            "mpsa_server_destroy", "mpsa_server_cancel_queued",
+            "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy"]
+REQ_SPECTRUM, REQ_ODF = 1, 2
 KERNEL_PROFILE, KERNEL_ODF = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -48,6 +52,30 @@ class SynthOpts(C.Structure):
 
 class Atmos(C.Structure):
     _fields_ = [("n_depth", C.c_int32), ("m", _dp), ("T", _dp), ("P", _dp), ("comp", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("atm", Atmos), ("win", LGrid), ("n_mu", C.c_int32), ("mu", _dp),
+                ("I_out", _fp), ("n_sel", C.c_int32), ("sel", _ip), ("grid", LGrid), ("K", C.c_int32),
+                ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", _dp),
+                ("kappa_c_out", _fp)]
+
+
+class BatchGroup(C.Structure):
+    _fields_ = [("grid", LGrid), ("n_sel", C.c_int32), ("sel", _ip), ("kappa_out", C.c_void_p),
+                ("kappa_c_out", C.c_void_p), ("evals_out", C.c_void_p), ("K", C.c_int32),
+                ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("pts_per_thread", C.c_int32), ("threads", C.c_int32), ("min_blocks", C.c_int32),
+                ("n_rows", C.c_int32), ("n_units", C.c_int64), ("n_tuned", C.c_int32),
+                ("tune_ms_per_mpoint", C.c_double * 8)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("running", C.c_int64),
+                ("queued", C.c_int64), ("bytes_in_use", C.c_size_t), ("bytes_peak", C.c_size_t)]
 
 
 class MpsaError(RuntimeError):
@@ -85,6 +113,24 @@ def load_library(path: str = LIB_PATH):
     lib.build_odf_noalloc.argtypes = [C.c_int32, vp, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.c_int32,
                                       _dp, C.c_int32, vp, vp]
     lib.build_odf_noalloc.restype = C.c_int
+    lib.mpsa_server_create.argtypes = [C.POINTER(vp), vp, C.c_size_t, C.c_int32, C.c_int32]
+    lib.mpsa_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_int64)]
+    lib.mpsa_server_wait.argtypes = [vp, C.c_int64, C.c_int32, C.POINTER(C.c_double)]
+    lib.mpsa_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    lib.mpsa_server_cancel_queued.argtypes = [vp, C.POINTER(C.c_int64)]
+    lib.mpsa_server_cancel_queued.restype = C.c_int
+    lib.mpsa_server_destroy.argtypes = [vp]
+    lib.mpsa_server_destroy.restype = None
+    for f in ("mpsa_server_create", "mpsa_server_submit", "mpsa_server_wait", "mpsa_server_get_stats"):
+        getattr(lib, f).restype = C.c_int
+    lib.mpsa_batch_create.argtypes = [vp, C.c_int32, C.POINTER(BatchGroup), C.POINTER(SynthOpts), C.c_int32, vp,
+                                      C.POINTER(vp)]
+    lib.mpsa_batch_run.argtypes = [vp, vp]
+    lib.mpsa_batch_get_info.argtypes = [vp, C.POINTER(BatchInfo)]
+    lib.mpsa_batch_destroy.argtypes = [vp]
+    lib.mpsa_batch_destroy.restype = None
+    for f in ("mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info"):
+        getattr(lib, f).restype = C.c_int
     lib.mpsa_profile_enable.argtypes = [vp, C.c_int]
     lib.mpsa_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     for f in ("mpsa_create", "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
@@ -228,3 +274,143 @@ class Context:
         o = opts if opts is not None else make_opts()
         _check(self.lib.synth_spectrum(self.h, C.byref(a), C.byref(g), len(mu), _ptr(mu, C.c_double), _dev(I_out),
                                        C.byref(o), _stream(stream)))
+
+
+class Server:
+    """Continuous-batching request server on a Context (see mpsa_server_* in include/mpsa.h).
+
+    submit_spectrum / submit_odf copy their inputs and return a ticket; wait(ticket) returns
+    the result (numpy array(s)) and the latency in ms.  The context must not be used
+    directly while the server exists.
+    """
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_inflight: int = 4, rows_per_chunk: int = 8):
+        self.lib = ctx.lib
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(self.lib.mpsa_server_create(C.byref(h), ctx.h, int(hbm_budget_bytes), int(max_inflight),
+                                           int(rows_per_chunk)))
+        self.h = h
+        self._pending = {}
+
+    def submit_spectrum(self, m, T, P, win, mus, comp=0):
+        m = _arr(m, np.float64); T = _arr(T, np.float64); P = _arr(P, np.float64); mu = _arr(mus, np.float64)
+        N = grid_size(win.lam0_nm, win.lam1_nm, win.R)
+        out = np.empty((len(mu), N), dtype=np.float32)
+        q = Request()
+        q.kind = REQ_SPECTRUM
+        q.atm = Atmos(len(m), _ptr(m, C.c_double), _ptr(T, C.c_double), _ptr(P, C.c_double), int(comp))
+        q.win = LGrid(win.lam0_nm, win.lam1_nm, win.R)
+        q.n_mu = len(mu)
+        q.mu = _ptr(mu, C.c_double)
+        q.I_out = _ptr(out, C.c_float)
+        t = C.c_int64()
+        _check(self.lib.mpsa_server_submit(self.h, C.byref(q), C.byref(t)))
+        self._pending[t.value] = (out,)
+        return t.value
+
+    def submit_odf(self, sel, grid, bounds, widths):
+        s = _arr(sel, np.int32); b = _arr(bounds, np.int64); w = _arr(widths, np.float64)
+        out = np.empty((len(s), len(b) - 1, len(w)), dtype=np.float64)
+        kc = np.empty(len(s), dtype=np.float32)
+        q = Request()
+        q.kind = REQ_ODF
+        q.n_sel = len(s)
+        q.sel = _ptr(s, C.c_int32)
+        q.grid = LGrid(grid.lam0_nm, grid.lam1_nm, grid.R)
+        q.K = len(b) - 1
+        q.bounds = _ptr(b, C.c_int64)
+        q.n_steps = len(w)
+        q.widths = _ptr(w, C.c_double)
+        q.odf_out = _ptr(out, C.c_double)
+        q.kappa_c_out = _ptr(kc, C.c_float)
+        t = C.c_int64()
+        _check(self.lib.mpsa_server_submit(self.h, C.byref(q), C.byref(t)))
+        self._pending[t.value] = (out, kc)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=600_000):
+        lat = C.c_double()
+        _check(self.lib.mpsa_server_wait(self.h, int(ticket), int(timeout_ms), C.byref(lat)))
+        res = self._pending.pop(ticket)
+        return (res[0] if len(res) == 1 else res), lat.value
+
+    def cancel_queued(self):
+        n = C.c_int64()
+        _check(self.lib.mpsa_server_cancel_queued(self.h, C.byref(n)))
+        return n.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(self.lib.mpsa_server_get_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.mpsa_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Persistent, graph-captured batch of row groups (see mpsa_batch_* in include/mpsa.h).
+
+    groups: list of dicts with keys grid, sel, kappa (CUDA tensor [n_sel][N]) and optionally
+    kappa_c, evals (CUDA tensors), bounds, widths, odf (CUDA tensor [n_sel][K][n_steps])."""
+
+    def __init__(self, ctx: Context, groups, opts=None, autotune=True, stream=None):
+        self.lib = ctx.lib
+        self._keep = []
+        arr = (BatchGroup * len(groups))()
+        for i, g in enumerate(groups):
+            sel = _arr(g["sel"], np.int32)
+            self._keep.append(sel)
+            q = arr[i]
+            q.grid = LGrid(g["grid"].lam0_nm, g["grid"].lam1_nm, g["grid"].R)
+            q.n_sel = len(sel)
+            q.sel = _ptr(sel, C.c_int32)
+            q.kappa_out = _dev(g["kappa"])
+            q.kappa_c_out = _dev(g.get("kappa_c"))
+            q.evals_out = _dev(g.get("evals"))
+            if g.get("odf") is not None:
+                b = _arr(g["bounds"], np.int64)
+                w = _arr(g["widths"], np.float64)
+                self._keep += [b, w]
+                q.K = len(b) - 1
+                q.bounds = _ptr(b, C.c_int64)
+                q.n_steps = len(w)
+                q.widths = _ptr(w, C.c_double)
+                q.odf_out = _dev(g["odf"])
+            else:
+                q.K = 0
+        o = opts if opts is not None else make_opts()
+        h = C.c_void_p()
+        _check(self.lib.mpsa_batch_create(ctx.h, len(groups), arr, C.byref(o), 1 if autotune else 0, _stream(stream),
+                                          C.byref(h)))
+        self.h = h
+
+    def run(self, stream=None):
+        _check(self.lib.mpsa_batch_run(self.h, _stream(stream)))
+
+    def info(self):
+        i = BatchInfo()
+        _check(self.lib.mpsa_batch_get_info(self.h, C.byref(i)))
+        return {"pts_per_thread": i.pts_per_thread, "threads": i.threads, "min_blocks": i.min_blocks,
+                "n_rows": i.n_rows, "n_units": i.n_units,
+                "tune_ms_per_mpoint": [i.tune_ms_per_mpoint[k] for k in range(i.n_tuned)]}
+
+    def close(self):
+        if self.h:
+            self.lib.mpsa_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace mpsa {
 

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace mpsa {
 
@@ -43,6 +44,7 @@ struct Target {
     long long k;                 // rank (0-based) of the order statistic
     long long cnt_lt;            // values below the current prefix range
     unsigned long long iv_lt;    // exact sum (group units) of the group's values below the prefix range
+    long long cnt_in;            // values inside the current prefix range
     unsigned prefix;             // bits resolved so far
     int slot;                    // distinct-prefix slot at the current level
     int total;                   // 1 when k >= n (S is the total)
@@ -50,46 +52,55 @@ struct Target {
 
 __device__ __forceinline__ unsigned long long group_base(unsigned E) { return E >= 1 ? (1ull << 23) : 0ull; }
 
-// Visit every value of x[0..n) once, 16-byte vector loads for the aligned body.
+// Visit every value of x[0..n) once.  Thread t walks a contiguous chunk of the
+// 16-byte-aligned body (so that runs of neighbouring grid points stay in one thread),
+// then the unaligned head and tail.  Every thread makes the same number of calls
+// f(bits, valid), so warp-wide votes inside f are safe.
 template <class F>
 __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long long n, F&& f) {
     const int tid = threadIdx.x;
     const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
     long long head = mis ? (long long)(4u - mis) : 0;
     if (head > n) head = n;
-    if (tid < head) f(__float_as_uint(__ldg(x + tid)));
     const float4* body = reinterpret_cast<const float4*>(x + head);
     const long long nv = (n - head) >> 2;
-    for (long long i = tid; i < nv; i += kOdfThreads) {
-        const float4 q = __ldg(body + i);
-        f(__float_as_uint(q.x));
-        f(__float_as_uint(q.y));
-        f(__float_as_uint(q.z));
-        f(__float_as_uint(q.w));
+    const long long per = (nv + kOdfThreads - 1) / kOdfThreads;
+    const long long i0 = (long long)tid * per;
+    for (long long it = 0; it < per; ++it) {
+        const long long i = i0 + it;
+        const bool v = i < nv;
+        const float4 q = v ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        f(__float_as_uint(q.x), v);
+        f(__float_as_uint(q.y), v);
+        f(__float_as_uint(q.z), v);
+        f(__float_as_uint(q.w), v);
     }
     const long long t0 = head + (nv << 2);
-    if (t0 + tid < n) f(__float_as_uint(__ldg(x + t0 + tid)));
+    f(tid < head ? __float_as_uint(__ldg(x + tid)) : 0u, tid < head);
+    f(t0 + tid < n ? __float_as_uint(__ldg(x + t0 + tid)) : 0u, t0 + tid < n);
 }
 
-// Histogram add aggregated over a warp: neighbouring grid points usually fall into the
-// same bin, and 32 lanes adding to one shared address serialise.  A segmented scan over
-// runs of equal keys (Hillis-Steele with head flags) sums each run, and only the last lane
-// of a run issues the atomic.  key < 0 means "nothing to add".  All 32 lanes must call.
-__device__ __forceinline__ void warp_hist_add(unsigned long long* __restrict__ h, int key, unsigned long long val,
-                                              int lane) {
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const int next = __shfl_down_sync(0xffffffffu, key, 1);
-    bool flag = lane == 0 || prev != key;
-    const bool tail = lane == 31 || next != key;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, val, d);
-        const bool g = __shfl_up_sync(0xffffffffu, flag, d);
-        if (lane >= d && !flag) val += y;
-        if (lane >= d) flag = flag || g;
+// Per-thread run merging of histogram adds: consecutive values of a thread's chunk
+// usually fall into the same bin; they are summed in registers and one shared-memory
+// atomic is issued per run.
+struct RunAdd {
+    int key = -1;
+    unsigned long long val = 0;
+    __device__ __forceinline__ void add(unsigned long long* __restrict__ h, int k, unsigned long long v) {
+        if (k == key) {
+            val += v;
+        } else {
+            if (key >= 0) atomicAdd(&h[key], val);
+            key = k;
+            val = v;
+        }
     }
-    if (tail && key >= 0) atomicAdd(&h[key], val);
-}
+    __device__ __forceinline__ void flush(unsigned long long* __restrict__ h) {
+        if (key >= 0) atomicAdd(&h[key], val);
+        key = -1;
+        val = 0;
+    }
+};
 
 // One warp resolves one target inside its slot's 2^wb-bin histogram h (packed counts and
 // low-bit sums): finds the sub-bin holding rank t.k and adds the counts and exact sums
@@ -140,6 +151,7 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
     if (lane == 0) {
         t.iv_lt += ivs;
         t.cnt_lt = cnt_below;
+        t.cnt_in = (long long)(h[found] >> 40);
         t.prefix |= (unsigned)found << sh;
     }
 }
@@ -155,6 +167,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     unsigned long long* h2 = sm + kL1Bins;                   // [nslots][256]; its first 8 KB double as cbefore
     int* cbefore = reinterpret_cast<int*>(h2);               // [2048] (only before the levels)
     unsigned* cand = reinterpret_cast<unsigned*>(h2 + (size_t)nslots * 256);   // [kCand]
+    short* slot2 = reinterpret_cast<short*>(cand + kCand);   // [nslots][256]: depth-19 prefix -> slot
     __shared__ short slot1[kL1Bins];
     __shared__ unsigned long long gsum[256];
     __shared__ double gpre[257];
@@ -177,33 +190,14 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     // ---- pass 1 (HBM): level-1 histogram with exact low-bit sums
     long long zeros = 0;
     {
-        auto one = [&](unsigned bits, bool valid) {
+        RunAdd run;
+        for_each_value(x, n, [&](unsigned bits, bool valid) {
+            if (!valid) return;
             bits &= 0x7fffffffu;
-            const bool use = valid && bits != 0u;
-            if (valid && bits == 0u) ++zeros;
-            warp_hist_add(h1, use ? (int)(bits >> 20) : -1, kOne | (unsigned long long)(bits & 0xfffffu), lane);
-        };
-        const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
-        long long head = mis ? (long long)(4u - mis) : 0;
-        if (head > n) head = n;
-        const float4* body = reinterpret_cast<const float4*>(x + head);
-        const long long nv = (n - head) >> 2;
-        const long long t0 = head + (nv << 2);
-        // head and tail (< 4 values each) by the first warp
-        if (warp == 0) {
-            one(lane < head ? __float_as_uint(__ldg(x + lane)) : 0u, lane < head);
-            one(t0 + lane < n ? __float_as_uint(__ldg(x + t0 + lane)) : 0u, t0 + lane < n);
-        }
-        // body: whole warps iterate together so that every lane takes part in the scans
-        const long long span = ((nv + kOdfThreads - 1) / kOdfThreads) * kOdfThreads;
-        for (long long i = tid; i < span; i += kOdfThreads) {
-            const bool v = i < nv;
-            float4 q = v ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            one(__float_as_uint(q.x), v);
-            one(__float_as_uint(q.y), v);
-            one(__float_as_uint(q.z), v);
-            one(__float_as_uint(q.w), v);
-        }
+            if (bits == 0u) { ++zeros; return; }
+            run.add(h1, (int)(bits >> 20), kOne | (unsigned long long)(bits & 0xfffffu));
+        });
+        run.flush(h1);
     }
     for (int d = 16; d > 0; d >>= 1) zeros += __shfl_down_sync(0xffffffffu, zeros, d);
     if (lane == 0 && zeros) atomicAdd((unsigned long long*)&s_zero, (unsigned long long)zeros);
@@ -244,11 +238,13 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     }
     if (tid < nt) {
         Target t;
-        t.k = (long long)floor(cw[tid + 1] * (double)n);
+        // u = c_s n rounded to FP64 exactly as written (no fused multiply-add), as the reference does
+        t.k = (long long)floor(__dmul_rn(cw[tid + 1], (double)n));
         t.total = t.k >= n;
         t.slot = -1;
         t.prefix = 0;
         t.cnt_lt = 0;
+        t.cnt_in = 0;
         t.iv_lt = 0;
         tg[tid] = t;
     }
@@ -283,6 +279,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             if (c > 0 && cbefore[bb] <= kk && kk < cbefore[bb] + c) {
                 tg[t].prefix = (unsigned)bb << 20;
                 tg[t].cnt_lt = cbefore[bb];
+                tg[t].cnt_in = c;
                 unsigned long long acc = 0;
                 for (int m = bb & ~7; m < bb; ++m) {
                     const unsigned long long h = h1[m];
@@ -293,78 +290,99 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        int nd = 0;
-        for (int t = 0; t < nt; ++t) {
-            if (tg[t].total) continue;
-            const int b = (int)(tg[t].prefix >> 20);
-            if (slot1[b] < 0) slot1[b] = (short)nd++;
-        }
-        n_distinct = nd;
-    }
-    __syncthreads();
-
-    // ---- pass 2 (L2): candidates = non-zero values in a target's level-1 bin
-    if (n_distinct > 0) {
-        for_each_value(x, n, [&](unsigned bits) {
-            bits &= 0x7fffffffu;
-            const bool c = bits != 0u && slot1[bits >> 20] >= 0;
-            const unsigned act = __activemask();
-            const unsigned bal = __ballot_sync(act, c);
-            if (!c) return;
-            const int leader = __ffs(bal) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&n_cand, __popc(bal));
-            base = __shfl_sync(bal, base, leader);
-            const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (pos < kCand) cand[pos] = bits;
-        });
-    }
-    __syncthreads();
-    const int nc = n_cand;
-    const bool in_smem = nc <= kCand;
-
-    // ---- levels 2..4 on the candidates (or on the interval again if they overflowed)
+    // ---- levels 2..4.  The counts of the current target prefixes are known from the last
+    // histogram; once they fit the candidate buffer, one pass (from L2) collects those
+    // values and every remaining level runs on the buffer.  Until then each level is a
+    // histogram pass over the interval (from L2) restricted to the target prefixes, found
+    // with O(1) prefix -> slot tables (slot1 at 11 resolved bits, slot2 at 19).
     const int shifts[3] = {12, 4, 0};
     const int widths[3] = {8, 8, 4};
+    bool have_cand = false;
+    int nc = 0;
+    int nd_prev = 0;
     for (int lvl = 0; lvl < 3; ++lvl) {
         const int sh = shifts[lvl], wb = widths[lvl];
         const int hiShift = sh + wb;
         const int nbins = 1 << wb;
         if (tid == 0) {
             int nd = 0;
+            long long tot_in = 0;
             for (int t = 0; t < nt; ++t) {
                 if (tg[t].total) continue;
                 int f = -1;
                 for (int q = 0; q < nd; ++q)
                     if (dpre[q] == tg[t].prefix) f = q;
-                if (f < 0) { dpre[nd] = tg[t].prefix; f = nd++; }
+                if (f < 0) {
+                    dpre[nd] = tg[t].prefix;
+                    f = nd++;
+                    tot_in += tg[t].cnt_in - (tg[t].prefix == 0u ? s_zero : 0);
+                }
                 tg[t].slot = f;
             }
             n_distinct = nd;
+            n_cand = (!have_cand && tot_in <= kCand) ? 0 : -1;   // 0: collect in this level
         }
         __syncthreads();
         const int nd = n_distinct;
+        if (nd == 0) break;
+        const bool collect = n_cand == 0;
+        // prefix -> slot tables for the current depth
+        if (lvl == 0) {
+            for (int q = tid; q < nd; q += kOdfThreads) slot1[dpre[q] >> 20] = (short)q;
+        } else if (lvl == 1) {
+            for (int i = tid; i < nd_prev * 256; i += kOdfThreads) slot2[i] = -1;
+        }
+        __syncthreads();
+        if (lvl == 1)
+            for (int q = tid; q < nd; q += kOdfThreads) {
+                const int q1 = slot1[dpre[q] >> 20];
+                if (q1 >= 0) slot2[q1 * 256 + ((dpre[q] >> 12) & 255u)] = (short)q;
+            }
         for (int i = tid; i < nd * 256; i += kOdfThreads) h2[i] = 0ull;
         __syncthreads();
-        auto add = [&](unsigned bits) {
+        // slot of a value at the current depth, or -1 (zeros are never in a slot)
+        auto slot_of = [&](unsigned bits) -> int {
+            if (bits == 0u) return -1;
+            const int q1 = slot1[bits >> 20];
+            if (q1 < 0 || lvl == 0) return q1;
+            if (lvl == 1) return slot2[q1 * 256 + ((bits >> 12) & 255u)];
             const unsigned pre = (bits >> hiShift) << hiShift;
             int q = -1;
             for (int r = 0; r < nd; ++r)
                 if (dpre[r] == pre) q = r;
-            if (q < 0) return;
-            const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
-            const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
-            atomicAdd(&h2[q * 256 + sub], kOne | low);
+            return q;
         };
-        if (in_smem) {
-            for (int i = tid; i < nc; i += kOdfThreads) add(cand[i]);
-        } else {
-            for_each_value(x, n, [&](unsigned bits) {
+        if (collect) {
+            for_each_value(x, n, [&](unsigned bits, bool valid) {
                 bits &= 0x7fffffffu;
-                if (bits == 0u || slot1[bits >> 20] < 0) return;
-                add(bits);
+                if (!valid || slot_of(bits) < 0) return;
+                const int pos = atomicAdd(&n_cand, 1);
+                if (pos < kCand) cand[pos] = bits;
             });
+            __syncthreads();
+            nc = min(n_cand, kCand);
+            have_cand = true;
+        }
+        if (have_cand) {
+            for (int i = tid; i < nc; i += kOdfThreads) {
+                const unsigned bits = cand[i];
+                const int q = slot_of(bits);
+                if (q < 0) continue;
+                const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
+                const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
+                atomicAdd(&h2[q * 256 + sub], kOne | low);
+            }
+        } else {
+            RunAdd run;
+            for_each_value(x, n, [&](unsigned bits, bool valid) {
+                bits &= 0x7fffffffu;
+                const int q = valid ? slot_of(bits) : -1;
+                if (q < 0) return;
+                const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
+                const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
+                run.add(h2, q * 256 + (int)sub, kOne | low);
+            });
+            run.flush(h2);
         }
         __syncthreads();
         if (tid < nd && dpre[tid] == 0u) h2[tid * 256] += (unsigned long long)s_zero << 40;
@@ -375,6 +393,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             resolve_warp(tt, h2 + tt.slot * 256, wb, sh, lane);
             if (lane == 0) tg[t] = tt;
         }
+        nd_prev = nd;
         __syncthreads();
     }
 
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             const double unit = ldexp(1.0, (E >= 1 ? (int)E : 1) - 150);
             const double theta = (double)__uint_as_float(t.prefix);
             const double below = gpre[E] + (double)t.iv_lt * unit;
-            const double u = cw[bidx] * (double)n;
+            const double u = __dmul_rn(cw[bidx], (double)n);   // rounded product: no contraction into u - cnt_lt
             return below + (u - (double)t.cnt_lt) * theta;
         };
         out[((size_t)row * K + k) * n_steps + s] = (S(s + 1) - S(s)) / (w[s] * (double)n);
@@ -400,7 +419,8 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
 size_t odf_smem_bytes(int n_steps) {
     const int nt = n_steps - 1;
     const int nslots = nt > 4 ? nt : 4;
-    return (kL1Bins + (size_t)nslots * 256) * sizeof(unsigned long long) + kCand * sizeof(unsigned);
+    return (kL1Bins + (size_t)nslots * 256) * sizeof(unsigned long long) + kCand * sizeof(unsigned) +
+           (size_t)nslots * 256 * sizeof(short);
 }
 
 }  // namespace
@@ -409,10 +429,10 @@ size_t odf_smem_bytes(int n_steps) {
 
 using namespace mpsa;
 
-extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N, int32_t K,
-                         const int64_t* bounds, int32_t n_steps, const double* widths, int32_t mean_kind,
-                         double* odf_out, void* stream) {
-    if (!ctx || !kappa || !bounds || !widths || !odf_out) return fail(MPSA_EINVAL, "build_odf: NULL argument");
+namespace mpsa {
+
+int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, const double* widths, int mean_kind,
+              double* cw) {
     if (n_rows < 1 || N < 1 || K < 1) return fail(MPSA_EINVAL, "build_odf: n_rows %d N %lld K %d", n_rows, (long long)N, K);
     if (n_steps < 1 || n_steps > kMaxSteps) return fail(MPSA_EINVAL, "build_odf: n_steps = %d (1..%d)", n_steps, kMaxSteps);
     if (mean_kind != MPSA_MEAN_ARITH)
@@ -424,7 +444,6 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
         if (len >= (1 << 21)) return fail(MPSA_EINVAL, "build_odf: interval %d has %lld points (max 2^21-1)", k, (long long)len);
     }
     // cumulative widths: FP64 left-to-right partial sums, the last forced to 1
-    std::vector<double> cw(n_steps + 1);
     double acc = 0.0;
     cw[0] = 0.0;
     for (int s = 0; s < n_steps; ++s) {
@@ -434,28 +453,53 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     }
     if (fabs(acc - 1.0) > 1e-12) return fail(MPSA_EINVAL, "build_odf: widths sum to %.17g", acc);
     cw[n_steps] = 1.0;
+    return MPSA_OK;
+}
+
+int odf_setup() {
+    int dev = 0;
+    MPSA_CUDA_TRY(cudaGetDevice(&dev));
+    static unsigned attr_set = 0;   // one bit per device
+    if (!(attr_set & (1u << (dev & 31)))) {
+        MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)odf_smem_bytes(kMaxSteps)));
+        attr_set |= 1u << (dev & 31);
+    }
+    return MPSA_OK;
+}
+
+int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* d_bounds, int n_steps,
+               const double* d_cw, const double* d_w, double* d_out, cudaStream_t st) {
+    int r;
+    if ((r = odf_setup())) return r;
+    k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w,
+                                                                         d_out);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
+
+}  // namespace mpsa
+
+extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N, int32_t K,
+                         const int64_t* bounds, int32_t n_steps, const double* widths, int32_t mean_kind,
+                         double* odf_out, void* stream) {
+    if (!ctx || !kappa || !bounds || !widths || !odf_out) return fail(MPSA_EINVAL, "build_odf: NULL argument");
+    std::vector<double> cw(n_steps >= 1 && n_steps <= kMaxSteps ? n_steps + 1 : 1);
+    int r;
+    if ((r = odf_check(n_rows, N, K, bounds, n_steps, widths, mean_kind, cw.data()))) return r;
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc(st);
     int64_t* d_b;
     double *d_cw, *d_w;
-    int r;
     if ((r = sc.alloc(&d_b, K + 1)) || (r = sc.alloc(&d_cw, n_steps + 1)) || (r = sc.alloc(&d_w, n_steps))) return r;
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_b, bounds, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_cw, cw.data(), (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_w, widths, n_steps * sizeof(double), cudaMemcpyHostToDevice, st));
-    const size_t smem = odf_smem_bytes(n_steps);
-    static unsigned attr_set = 0;   // one bit per device
-    if (!(attr_set & (1u << (ctx->device & 31)))) {
-        MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)odf_smem_bytes(kMaxSteps)));
-        attr_set |= 1u << (ctx->device & 31);
-    }
     prof_mark(ctx, MPSA_KERNEL_ODF, st);
-    k_odf<<<dim3(K, n_rows), kOdfThreads, smem, st>>>(kappa, N, K, d_b, n_steps, d_cw, d_w, odf_out);
+    r = odf_launch(kappa, n_rows, N, K, d_b, n_steps, d_cw, d_w, odf_out, st);
     prof_mark(ctx, MPSA_KERNEL_ODF, st);
-    MPSA_CUDA_TRY(cudaGetLastError());
-    return MPSA_OK;
+    return r;
 }
 
 // ---------------------------------------------------------------------------

@@ -13,14 +13,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace mpsa {
-
-int populations_device(int n_el, const double* d_el, const double* d_abund, int n_comp, int n_points,
-                       const double* d_T, const double* d_P, double* d_pop, cudaStream_t s);
-int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
-               float* kappa, float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st);
-int check_grid(const mpsa_lgrid* g, int* N);
 
 namespace {
 
@@ -74,6 +69,13 @@ __global__ void k_iota(int n, int* p) {
 unsigned g_spec_init = 0;
 
 }  // namespace
+
+int formal_launch(int D, int N, const float* kappa, const float* kc, const float* m, const float* T, double lam0_nm,
+                  double lnq, int n_mu, const float* mu, float* I_out, cudaStream_t st) {
+    k_formal<<<(N + 127) / 128, 128, 0, st>>>(D, N, kappa, kc, m, T, lam0_nm, lnq, n_mu, mu, I_out);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
 
 int spectrum_module_init(int device) {
     g_spec_init |= 1u << (device & 31);
@@ -132,9 +134,7 @@ extern "C" int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_l
     if ((r = populations_device(ne, ctx->d_el, dab, 1, D, dT, dP, dpop, st))) return r;
     k_iota<<<(D + 127) / 128, 128, 0, st>>>(D, dsel);
     if ((r = synth_rows(ctx, dpop, D, dsel, win->lambda0_nm, win->R, N, kap, kc, nullptr, opts, st))) return r;
-    k_formal<<<(N + 127) / 128, 128, 0, st>>>(D, N, kap, kc, fm, fT, win->lambda0_nm, log1p(1.0 / win->R), n_mu, fmu,
-                                              I_out);
-    MPSA_CUDA_TRY(cudaGetLastError());
+    if ((r = formal_launch(D, N, kap, kc, fm, fT, win->lambda0_nm, log1p(1.0 / win->R), n_mu, fmu, I_out, st))) return r;
     // pageable host-to-device copies are staged before cudaMemcpyAsync returns,
     // so the host vectors above may go out of scope now
     return MPSA_OK;

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "voigt.cuh"
+#include "internal.cuh"
 
 namespace mpsa {
 
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t L, int N, const unsigne
 
 // k_ranges: cum[s][b][ts] = position of the first line of class b whose centre key is
 // >= (ts - 1) * kTile, ts = 0 .. nT + 2 (tiles -1 .. nT, with off-grid centres clamped).
-__global__ void k_ranges(int n_sel, int64_t L, int nT, const int* __restrict__ bkey,
+__global__ void k_ranges(int n_sel, int64_t L, int nT, int tile, const int* __restrict__ bkey,
                          const int* __restrict__ classbase, const int* __restrict__ classcnt, int* __restrict__ cum) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int W = nT + 3;
@@ -395,7 +396,7 @@ __global__ void k_ranges(int n_sel, int64_t L, int nT, const int* __restrict__ b
     const int s = (int)(t / ((int64_t)W * kNumClasses));
     const int base = classbase[s * kNumClasses + b], n = classcnt[s * kNumClasses + b];
     const int* k = bkey + (size_t)s * L + base;
-    const long long thr = (long long)(ts - 1) * kTile;
+    const long long thr = (long long)(ts - 1) * tile;
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -405,11 +406,269 @@ __global__ void k_ranges(int n_sel, int64_t L, int nT, const int* __restrict__ b
 }
 
 // ---------------------------------------------------------------------------
-// The profile kernel.
+// The profile kernel.  A tile of PTS * THREADS grid points is processed by one CTA:
+// thread t owns the points J0 + k THREADS + t, k = 0..PTS-1.
+struct RowDesc {
+    int N, nT, tile;
+    float lnq, q1, q2, q3;      // expm1(-x)/(-x) ~ 1 + d (q1 + d (q2 + d q3)), x = d lnq
+    const float* ln_tp;         // ln of the cut threshold t_p (outputs are t_p * sum of s_rel H)
+    const int* cum;             // [kNumClasses][nT + 3]
+    const int* bidx;            // [L] bucketed line indices
+    const int* c;
+    const float* f;
+    const float* srel;
+    const float* a;
+    const float* kv;
+    const int* jlo;
+    const int* jhi;
+    const int* ilo;
+    const int* ihi;
+    float* out;                 // [N]
+};
+
+// flag bits of the per-line records in shared memory
+constexpr int kFlKloBits = 5;
+constexpr int kFlMask = (1 << kFlKloBits) - 1;
+constexpr int kFlChk = 1 << 10;      // points near the cut: test s_rel H >= 1
+constexpr int kFlAlt = 1 << 11;      // far: "y" form; near: expm1 series for v
+constexpr int kFlFull = 1 << 12;     // the window covers every slot of the tile
+
+struct NearRec {
+    float cf, f, klnq, a, srel, kv;
+    int flags;
+    int jlo, jhi;    // outer cut window (grid indices)
+    int pad[3];
+};
+
+// far line.  With v' = sqrt(2) v = G_k * (sqrt2 kv B) + sqrt2 kv E1 (exact expm1 split
+// around the tile start) and D = v'^2 + 2a^2 - 1 = 2|z|^2 - 1, the far tier is
+//   s_rel H = (2 sk D + 4 sk) / (D^2 + 8 a^2)        ("exact" form, sk = s_rel a/sqrt(pi)),
+// which is the one-level continued fraction without truncation: 5 FFMA + 1 reciprocal.
+// Where D^2 could overflow FP32 (|v| >= 1e9 somewhere in the tile) the "y" form
+// y = 1/D, s_rel H = sk y (2 + 4 y) is used; there 8 a^2 y^2 is far below 1e-8.
+// The PTS points are evaluated without branches so that their dependency chains
+// interleave; MASKED lines (partial coverage or points near the cut) select with a mask.
+// p = {sqrt2 kv B, sqrt2 kv E1, 2a^2 - 1, 8a^2}, q = {2 sk, 4 sk}.
+template <int PTS, bool YFORM, bool MASKED>
+__device__ __forceinline__ void far_line(const float4 p, const float2 q, int klo, int khi, bool chk,
+                                         const float (&G)[PTS], float (&part)[PTS]) {
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+        const float vp = fmaf(G[k], p.x, p.y);
+        const float D = fmaf(vp, vp, p.z);
+        float t, y;
+        if (YFORM) {
+            y = rcp_approx(D);
+            t = fmaf(q.y, y, q.x);
+        } else {
+            y = rcp_approx(fmaf(D, D, p.w));
+            t = fmaf(q.x, D, q.y);
+        }
+        if (MASKED) {
+            const float l = t * y;
+            bool ok = (k >= klo) & (k <= khi);
+            if (chk) ok = ok & (l >= 1.f);
+            part[k] += ok ? l : 0.f;
+        } else {
+            part[k] = fmaf(t, y, part[k]);
+        }
+    }
+}
+
+// near line: exact offset d = (j - c) - f and the expm1 series for v; the tiers of H
+// branch per point.  Lines that do not cover the whole tile are culled per warp in
+// 32-point segments (a warp's lanes own 32 consecutive points of each slot).
+template <int PTS, int THREADS, bool FULL, bool CHK>
+__device__ __forceinline__ void near_line(const NearRec& r, int seg0, bool series, const float (&jf)[PTS],
+                                          float q1, float q2, float q3, float lnq, float (&part)[PTS]) {
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+        if (!FULL) {
+            const int lo = seg0 + k * THREADS;
+            if (lo + 31 < r.jlo || lo > r.jhi) continue;
+        }
+        const float d = (jf[k] - r.cf) - r.f;
+        float v;
+        if (series) v = r.klnq * (d * fmaf(d, fmaf(d, fmaf(d, q3, q2), q1), 1.f));
+        else v = r.kv * expm1f(-d * lnq);
+        float l = r.srel * voigt_H_lean(v, r.a);
+        if (CHK) l = (l >= 1.f) ? l : 0.f;
+        part[k] += l;
+    }
+}
+
+// One tile of one row.  Called by the grid kernel (one tile per CTA) and by the
+// persistent kernel (a loop over a work list).
+template <int PREC, int PTS, int THREADS>
+__device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
+    constexpr int TILE = PTS * THREADS;
+    __shared__ float4 sFarA[THREADS];
+    __shared__ float4 sFarB[THREADS];
+    __shared__ NearRec sNear[THREADS];
+    __shared__ int sCnt[2][THREADS / 32];
+
+    const int J0 = tile * TILE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    float jf[PTS], G[PTS], sum[PTS], comp[PTS], part[PTS];
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+        const int off = k * THREADS + tid;
+        jf[k] = (float)(J0 + off);
+        G[k] = expm1f(-(float)off * g.lnq);
+        sum[k] = 0.f;
+        comp[k] = 0.f;
+        part[k] = 0.f;
+    }
+
+    for (int b = 0; b < kNumClasses; ++b) {
+        const int reach = 1 << b;
+        int tlo = floordiv(J0 - reach + 1, TILE), thi = floordiv(J0 + TILE - 1 + reach - 1, TILE);
+        tlo = max(tlo, -1);
+        thi = min(thi, g.nT);
+        if (tlo > thi) continue;
+        const int* cum = g.cum + (size_t)b * (g.nT + 3);
+        const int beg = cum[tlo + 1], end = cum[thi + 2];
+        for (int base = beg; base < end; base += THREADS) {
+            // ---- set-up: one candidate line per thread
+            const int pos = base + tid;
+            bool isFar = false, isNear = false;
+            float4 fa, fb;
+            NearRec nr;
+            if (pos < end) {
+                const int q = g.bidx[pos];
+                const int jlo = g.jlo[q], jhi = g.jhi[q];
+                if (jhi >= J0 && jlo <= J0 + TILE - 1) {
+                    const int c = g.c[q];
+                    const float f = g.f[q], kv = g.kv[q], a = g.a[q], srel = g.srel[q];
+                    const int klo = max(0, (jlo - J0) / THREADS), khi = min(PTS - 1, (jhi - J0) / THREADS);
+                    const int P0 = J0 + klo * THREADS, P1 = J0 + khi * THREADS + THREADS - 1;
+                    const bool check = !(g.ilo[q] <= P0 && g.ihi[q] >= P1);
+                    // distance from the centre x0 = c + f to the nearest point of the tile
+                    // (far lines are evaluated at all points, masked to [klo, khi])
+                    const int T0 = J0, T1 = J0 + TILE - 1;
+                    float dist;
+                    bool red;
+                    if (c + 1 <= T0) { dist = (float)(T0 - c) - f; red = true; }
+                    else if (c >= T1) { dist = f + (float)(c - T1); red = false; }
+                    else { dist = 0.f; red = true; }
+                    float vmin = 0.f;
+                    if (dist >= (float)kFarDist)
+                        vmin = red ? -kv * expm1f(-dist * g.lnq) : kv * expm1f(dist * g.lnq);
+                    const int flags = klo | (khi << kFlKloBits) | (check ? kFlChk : 0) |
+                                      ((klo == 0 && khi == PTS - 1) ? kFlFull : 0);
+                    if (dist >= (float)kFarDist && vmin >= kFarV) {
+                        isFar = true;
+                        const float D = (float)(J0 - c) - f;
+                        const float x = D * g.lnq;
+                        const float E1 = expm1f(-x), B = expf(-x);
+                        const float A = a * a;
+                        const float r2 = 1.41421356237309505f;
+                        // the largest |v| on the tile (both ends) decides between the two forms
+                        const float xe = ((float)(J0 + TILE - 1 - c) - f) * g.lnq;
+                        const float vmax = fmaxf(fabsf(kv * E1), fabsf(kv * expm1f(-xe)));
+                        const bool yform = vmax >= 1.0e9f;
+                        const float sk = srel * a * kInvSqrtPi;
+                        fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
+                        fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
+                    } else {
+                        isNear = true;
+                        const float dmax = fmaxf(fabsf((float)(P0 - c) - f), fabsf((float)(P1 - c) - f));
+                        const bool series = dmax * g.lnq <= 0.05f;
+                        nr.cf = (float)c;
+                        nr.f = f;
+                        nr.klnq = kv * g.lnq;
+                        nr.a = a;
+                        nr.srel = srel;
+                        nr.kv = kv;
+                        nr.flags = flags | (series ? kFlAlt : 0);
+                        nr.jlo = jlo;
+                        nr.jhi = jhi;
+                        nr.pad[0] = nr.pad[1] = nr.pad[2] = 0;
+                    }
+                }
+            }
+            const unsigned bf = __ballot_sync(0xffffffffu, isFar), bn = __ballot_sync(0xffffffffu, isNear);
+            if (lane == 0) {
+                sCnt[0][warp] = __popc(bf);
+                sCnt[1][warp] = __popc(bn);
+            }
+            __syncthreads();
+            int offF = 0, offN = 0, nFar = 0, nNear = 0;
+#pragma unroll
+            for (int w = 0; w < THREADS / 32; ++w) {
+                const int cf = sCnt[0][w], cn = sCnt[1][w];
+                if (w < warp) { offF += cf; offN += cn; }
+                nFar += cf;
+                nNear += cn;
+            }
+            const unsigned lt = (1u << lane) - 1u;
+            if (isFar) {
+                const int p = offF + __popc(bf & lt);
+                sFarA[p] = fa;
+                sFarB[p] = fb;
+            }
+            if (isNear) sNear[offN + __popc(bn & lt)] = nr;
+            __syncthreads();
+
+            // ---- evaluation: every thread, every compacted line, its PTS points
+            for (int r = 0; r < nFar; ++r) {
+                const float4 p = sFarA[r];
+                const float4 q4 = sFarB[r];
+                const float2 q = make_float2(q4.x, q4.y);
+                const int fl = __float_as_int(q4.z);
+                const int klo = fl & kFlMask, khi = (fl >> kFlKloBits) & kFlMask;
+                const bool chk = fl & kFlChk, yform = fl & kFlAlt;
+                const bool plain = (fl & kFlFull) && !chk;     // all points, no cut test
+                if (yform) {
+                    if (plain) far_line<PTS, true, false>(p, q, klo, khi, chk, G, part);
+                    else far_line<PTS, true, true>(p, q, klo, khi, chk, G, part);
+                } else {
+                    if (plain) far_line<PTS, false, false>(p, q, klo, khi, chk, G, part);
+                    else far_line<PTS, false, true>(p, q, klo, khi, chk, G, part);
+                }
+            }
+            const int seg0 = J0 + warp * 32;
+            for (int r = 0; r < nNear; ++r) {
+                const NearRec nrr = sNear[r];
+                const bool series = nrr.flags & kFlAlt;
+                const bool full = nrr.flags & kFlFull, chk = nrr.flags & kFlChk;
+                if (full) {
+                    if (chk) near_line<PTS, THREADS, true, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                    else near_line<PTS, THREADS, true, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                } else {
+                    if (chk) near_line<PTS, THREADS, false, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                    else near_line<PTS, THREADS, false, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
+                }
+            }
+            if (PREC == MPSA_PREC_FP32_COMPENSATED) {
+                // fold the chunk's FP32 partial sums into the Kahan-compensated totals
+#pragma unroll
+                for (int k = 0; k < PTS; ++k) {
+                    const float y = part[k] - comp[k];
+                    const float t = sum[k] + y;
+                    comp[k] = (t - sum[k]) - y;
+                    sum[k] = t;
+                    part[k] = 0.f;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const float tp = expf(*g.ln_tp);
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+        const int j = J0 + k * THREADS + tid;
+        const float tot = (PREC == MPSA_PREC_FP32_COMPENSATED) ? (sum[k] - comp[k]) : part[k];
+        if (j < g.N) g.out[j] = tp * tot;
+    }
+}
+
+// Grid form: one CTA per (row, tile); the rows of one call share the prep arrays.
 struct TileArgs {
     int N, nT;
     int64_t L;
-    float lnq, q1, q2, q3;      // expm1(-x)/(-x) ~ 1 + d (q1 + d (q2 + d q3)), x = d lnq
+    float lnq, q1, q2, q3;
     const int* cum;
     const int* bidx;
     const int* c;
@@ -425,58 +684,30 @@ struct TileArgs {
     float* out;
 };
 
-struct NearRec {
-    float cf, f, klnq, a, srel, kv;
-    int flags;       // klo | khi << 3 | check << 6 | series << 7 | full << 8
-    int jlo, jhi;    // outer cut window (grid indices)
-    int pad[3];
-};
-
-// far line: v = G_k * kvB + kvE1 (exact expm1 decomposition around the tile start),
-// H by the far tier with the 1/(1 + 8 a^2 y^2) factor only when a^2 is not negligible.
-// The 8 points are evaluated without branches so that their dependency chains
-// interleave; MASKED lines (partial coverage or points near the cut) select with a mask.
-template <bool EPS, bool MASKED>
-__device__ __forceinline__ void far_line(const float4 p, float A8, int klo, int khi, bool chk, const float (&G)[8],
-                                         float (&part)[8]) {
-#pragma unroll
-    for (int k = 0; k < kPtsPerThread; ++k) {
-        const float v = fmaf(G[k], p.x, p.y);
-        const float y = rcp_approx(fmaf(2.f * v, v, p.z));
-        float l = p.w * y * fmaf(4.f, y, 2.f);
-        if (EPS) {
-            const float e = A8 * y * y;
-            l *= fmaf(e, e - 1.f, 1.f);
-        }
-        if (MASKED) {
-            bool ok = (k >= klo) & (k <= khi);
-            if (chk) ok = ok & (l >= 1.f);
-            l = ok ? l : 0.f;
-        }
-        part[k] += l;
-    }
-}
-
-// near line: exact offset d = (j - c) - f and the expm1 series for v; the tiers of H
-// branch per point.  Lines that do not cover the whole tile are culled per warp in
-// 32-point segments (a warp's lanes own 32 consecutive points of each slot).
-template <bool FULL, bool CHK>
-__device__ __forceinline__ void near_line(const NearRec& r, int seg0, bool series, const float (&jf)[8],
-                                          float q1, float q2, float q3, float lnq, float (&part)[8]) {
-#pragma unroll
-    for (int k = 0; k < kPtsPerThread; ++k) {
-        if (!FULL) {
-            const int lo = seg0 + k * kTileThreads;
-            if (lo + 31 < r.jlo || lo > r.jhi) continue;
-        }
-        const float d = (jf[k] - r.cf) - r.f;
-        float v;
-        if (series) v = r.klnq * (d * fmaf(d, fmaf(d, fmaf(d, q3, q2), q1), 1.f));
-        else v = r.kv * expm1f(-d * lnq);
-        float l = r.srel * voigt_H_lean(v, r.a);
-        if (CHK) l = (l >= 1.f) ? l : 0.f;
-        part[k] += l;
-    }
+__device__ __forceinline__ RowDesc row_desc(const TileArgs& g, int s, int tile) {
+    const size_t sL = (size_t)s * g.L;
+    RowDesc r;
+    r.N = g.N;
+    r.nT = g.nT;
+    r.tile = tile;
+    r.lnq = g.lnq;
+    r.q1 = g.q1;
+    r.q2 = g.q2;
+    r.q3 = g.q3;
+    r.ln_tp = g.ln_tp + s;
+    r.cum = g.cum + (size_t)s * kNumClasses * (g.nT + 3);
+    r.bidx = g.bidx + sL;
+    r.c = g.c + sL;
+    r.f = g.f + sL;
+    r.srel = g.srel + sL;
+    r.a = g.a + sL;
+    r.kv = g.kv + sL;
+    r.jlo = g.jlo + sL;
+    r.jhi = g.jhi + sL;
+    r.ilo = g.ilo + sL;
+    r.ihi = g.ihi + sL;
+    r.out = g.out + (size_t)s * g.N;
+    return r;
 }
 
 #ifndef MPSA_TILES_MINB
@@ -484,163 +715,26 @@ __device__ __forceinline__ void near_line(const NearRec& r, int seg0, bool serie
 #endif
 template <int PREC>
 __global__ void __launch_bounds__(kTileThreads, MPSA_TILES_MINB) k_tiles(TileArgs g) {
-    __shared__ float4 sFarA[kTileThreads];
-    __shared__ float2 sFarB[kTileThreads];
-    __shared__ NearRec sNear[kTileThreads];
-    __shared__ int sCnt[2][kTileThreads / 32];
+    const RowDesc r = row_desc(g, blockIdx.y, kTile);
+    tile_body<PREC, kPtsPerThread, kTileThreads>(r, blockIdx.x);
+}
 
-    const int s = blockIdx.y;
-    const int tile = blockIdx.x;
-    const int J0 = tile * kTile;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const size_t sL = (size_t)s * g.L;
-
-    float jf[kPtsPerThread], G[kPtsPerThread], sum[kPtsPerThread], comp[kPtsPerThread], part[kPtsPerThread];
-#pragma unroll
-    for (int k = 0; k < kPtsPerThread; ++k) {
-        const int off = k * kTileThreads + tid;
-        jf[k] = (float)(J0 + off);
-        G[k] = expm1f(-(float)off * g.lnq);
-        sum[k] = 0.f;
-        comp[k] = 0.f;
-        part[k] = 0.f;
-    }
-
-    for (int b = 0; b < kNumClasses; ++b) {
-        const int reach = 1 << b;
-        int tlo = floordiv(J0 - reach + 1, kTile), thi = floordiv(J0 + kTile - 1 + reach - 1, kTile);
-        tlo = max(tlo, -1);
-        thi = min(thi, g.nT);
-        if (tlo > thi) continue;
-        const int* cum = g.cum + ((size_t)s * kNumClasses + b) * (g.nT + 3);
-        const int beg = cum[tlo + 1], end = cum[thi + 2];
-        for (int base = beg; base < end; base += kTileThreads) {
-            // ---- set-up: one candidate line per thread
-            const int pos = base + tid;
-            bool isFar = false, isNear = false;
-            float4 fa;
-            float2 fb;
-            NearRec nr;
-            if (pos < end) {
-                const size_t q = sL + (size_t)g.bidx[sL + pos];
-                const int jlo = g.jlo[q], jhi = g.jhi[q];
-                if (jhi >= J0 && jlo <= J0 + kTile - 1) {
-                    const int c = g.c[q];
-                    const float f = g.f[q], kv = g.kv[q], a = g.a[q], srel = g.srel[q];
-                    const int klo = max(0, (jlo - J0) >> 8), khi = min(kPtsPerThread - 1, (jhi - J0) >> 8);
-                    const int P0 = J0 + klo * kTileThreads, P1 = J0 + khi * kTileThreads + kTileThreads - 1;
-                    const bool check = !(g.ilo[q] <= P0 && g.ihi[q] >= P1);
-                    // distance from the centre x0 = c + f to the nearest point of the tile
-                    // (far lines are evaluated at all 8 points, masked to [klo, khi])
-                    const int T0 = J0, T1 = J0 + kTile - 1;
-                    float dist;
-                    bool red;
-                    if (c + 1 <= T0) { dist = (float)(T0 - c) - f; red = true; }
-                    else if (c >= T1) { dist = f + (float)(c - T1); red = false; }
-                    else { dist = 0.f; red = true; }
-                    float vmin = 0.f;
-                    if (dist >= (float)kFarDist)
-                        vmin = red ? -kv * expm1f(-dist * g.lnq) : kv * expm1f(dist * g.lnq);
-                    const int flags = klo | (khi << 3) | (check ? 64 : 0) | ((klo == 0 && khi == kPtsPerThread - 1) ? 256 : 0);
-                    if (dist >= (float)kFarDist && vmin >= kFarV) {
-                        isFar = true;
-                        const float D = (float)(J0 - c) - f;
-                        const float x = D * g.lnq;
-                        const float E1 = expm1f(-x), B = expf(-x);
-                        const float A = a * a;
-                        fa = make_float4(kv * B, kv * E1, fmaf(2.f, A, -1.f), srel * a * kInvSqrtPi);
-                        const bool eps = 8.f * A * (1.f / 9.0e6f) > 1e-8f;   // (2 |z|^2 - 1)^2 >= 9e6 here
-                        fb = make_float2(8.f * A, __int_as_float(flags | (eps ? 128 : 0)));
-                    } else {
-                        isNear = true;
-                        const float dmax = fmaxf(fabsf((float)(P0 - c) - f), fabsf((float)(P1 - c) - f));
-                        const bool series = dmax * g.lnq <= 0.05f;
-                        nr.cf = (float)c;
-                        nr.f = f;
-                        nr.klnq = kv * g.lnq;
-                        nr.a = a;
-                        nr.srel = srel;
-                        nr.kv = kv;
-                        nr.flags = flags | (series ? 128 : 0);
-                        nr.jlo = jlo;
-                        nr.jhi = jhi;
-                        nr.pad[0] = nr.pad[1] = nr.pad[2] = 0;
-                    }
-                }
-            }
-            const unsigned bf = __ballot_sync(0xffffffffu, isFar), bn = __ballot_sync(0xffffffffu, isNear);
-            if (lane == 0) {
-                sCnt[0][warp] = __popc(bf);
-                sCnt[1][warp] = __popc(bn);
-            }
-            __syncthreads();
-            int offF = 0, offN = 0, nFar = 0, nNear = 0;
-#pragma unroll
-            for (int w = 0; w < kTileThreads / 32; ++w) {
-                const int cf = sCnt[0][w], cn = sCnt[1][w];
-                if (w < warp) { offF += cf; offN += cn; }
-                nFar += cf;
-                nNear += cn;
-            }
-            const unsigned lt = (1u << lane) - 1u;
-            if (isFar) {
-                const int p = offF + __popc(bf & lt);
-                sFarA[p] = fa;
-                sFarB[p] = fb;
-            }
-            if (isNear) sNear[offN + __popc(bn & lt)] = nr;
-            __syncthreads();
-
-            // ---- evaluation: every thread, every compacted line, its 8 points
-            for (int r = 0; r < nFar; ++r) {
-                const float4 p = sFarA[r];
-                const float2 q = sFarB[r];
-                const int fl = __float_as_int(q.y);
-                const int klo = fl & 7, khi = (fl >> 3) & 7;
-                const bool chk = fl & 64, eps = fl & 128;
-                const bool plain = (fl & 256) && !chk;     // all 8 points, no cut test
-                if (eps) {
-                    if (plain) far_line<true, false>(p, q.x, klo, khi, chk, G, part);
-                    else far_line<true, true>(p, q.x, klo, khi, chk, G, part);
-                } else {
-                    if (plain) far_line<false, false>(p, q.x, klo, khi, chk, G, part);
-                    else far_line<false, true>(p, q.x, klo, khi, chk, G, part);
-                }
-            }
-            const int seg0 = J0 + warp * 32;
-            for (int r = 0; r < nNear; ++r) {
-                const NearRec nrr = sNear[r];
-                const bool series = nrr.flags & 128;
-                const bool full = nrr.flags & 256, chk = nrr.flags & 64;
-                if (full) {
-                    if (chk) near_line<true, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
-                    else near_line<true, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
-                } else {
-                    if (chk) near_line<false, true>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
-                    else near_line<false, false>(nrr, seg0, series, jf, g.q1, g.q2, g.q3, g.lnq, part);
-                }
-            }
-            if (PREC == MPSA_PREC_FP32_COMPENSATED) {
-                // fold the chunk's FP32 partial sums into the Kahan-compensated totals
-#pragma unroll
-                for (int k = 0; k < kPtsPerThread; ++k) {
-                    const float y = part[k] - comp[k];
-                    const float t = sum[k] + y;
-                    comp[k] = (t - sum[k]) - y;
-                    sum[k] = t;
-                    part[k] = 0.f;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const float tp = expf(g.ln_tp[s]);
-    float* out = g.out + (size_t)s * g.N;
-#pragma unroll
-    for (int k = 0; k < kPtsPerThread; ++k) {
-        const int j = J0 + k * kTileThreads + tid;
-        const float tot = (PREC == MPSA_PREC_FP32_COMPENSATED) ? (sum[k] - comp[k]) : part[k];
-        if (j < g.N) out[j] = tp * tot;
+// Persistent form: a fixed grid of CTAs pulls (row, tile) units from a work list
+// (ordered by decreasing estimated cost) through one global counter.
+template <int PREC, int PTS, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_tiles_persistent(const RowDesc* __restrict__ rows,
+                                                                   const int2* __restrict__ units, int n_units,
+                                                                   int* __restrict__ counter) {
+    __shared__ int s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= n_units) break;
+        const int2 rt = units[u];
+        const RowDesc r = rows[rt.x];
+        tile_body<PREC, PTS, THREADS>(r, rt.y);
     }
 }
 
@@ -659,78 +753,119 @@ int synth_module_init(int device) {
 
 // Shared by synth_opacity and synth_spectrum: synthesis for rows `sel` of a
 // population table `pop` onto grid (lam0, R, N); writes kappa [n_sel][N].
-int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
-               float* kappa, float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st) {
+// Device buffers of the line preparation of n_sel rows (one grid, one tile size).
+struct PrepBufs {
+    int64_t L = 0;
+    int n_sel = 0, N = 0, nT = 0, nb = 0, tile = kTile;
+    double lnq = 0.0;
+    int *c = nullptr, *bidx = nullptr, *bkey = nullptr, *blkcnt = nullptr, *classbase = nullptr, *classcnt = nullptr,
+        *cum = nullptr;
+    float *f = nullptr, *lamcm = nullptr, *lnS = nullptr, *av = nullptr, *lnk0 = nullptr, *ln_tp = nullptr;
+    RowConst* rc = nullptr;
+    SpConst* spc = nullptr;
+    long long* wpart = nullptr;
+    PrepOut po{};
+};
+
+// Allocate every prep buffer through `al` (stream-ordered scratch or persistent memory).
+template <class Alloc>
+int prep_alloc(PrepBufs& b, const mpsa_ctx* ctx, int n_sel, int N, double R, int tile, Alloc&& al) {
+    b.L = ctx->L;
+    b.n_sel = n_sel;
+    b.N = N;
+    b.tile = tile;
+    b.nT = (N + tile - 1) / tile;
+    b.nb = (int)((b.L + 255) / 256);
+    b.lnq = log1p(1.0 / R);
+    const int64_t L = b.L;
+    const size_t SL = (size_t)n_sel * L;
+    int r;
+    if ((r = al(&b.c, L)) || (r = al(&b.f, L)) || (r = al(&b.lamcm, L)) || (r = al(&b.rc, n_sel)) ||
+        (r = al(&b.spc, (size_t)n_sel * ctx->n_sp)) || (r = al(&b.lnS, SL)) || (r = al(&b.av, SL)) ||
+        (r = al(&b.lnk0, SL)) || (r = al(&b.ln_tp, n_sel)) || (r = al(&b.po.c, SL)) || (r = al(&b.po.f, SL)) ||
+        (r = al(&b.po.srel, SL)) || (r = al(&b.po.a, SL)) || (r = al(&b.po.kv, SL)) || (r = al(&b.po.jlo, SL)) ||
+        (r = al(&b.po.jhi, SL)) || (r = al(&b.po.ilo, SL)) || (r = al(&b.po.ihi, SL)) || (r = al(&b.po.cls, SL)) ||
+        (r = al(&b.blkcnt, (size_t)n_sel * kNumClasses * b.nb)) || (r = al(&b.wpart, (size_t)n_sel * b.nb)) ||
+        (r = al(&b.classbase, (size_t)n_sel * kNumClasses)) || (r = al(&b.classcnt, (size_t)n_sel * kNumClasses)) ||
+        (r = al(&b.bidx, SL)) || (r = al(&b.bkey, SL)) || (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))))
+        return r;
+    b.po.blkcnt = b.blkcnt;
+    b.po.wpart = b.wpart;
+    return MPSA_OK;
+}
+
+int ranges_launch(const PrepBufs& b, int tile, int* cum, cudaStream_t st);
+
+// Line preparation of the rows d_sel of `pop` on the grid (lam0, R, N): placement, line terms,
+// median continuum and cut threshold, cut windows, width-class buckets and tile ranges.
+int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const int* d_sel, double lam0_nm,
+                float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st) {
     const double cut = (opts && opts->cut > 0) ? opts->cut : 1e-3;
     const double kcf = (opts && opts->kc_factor > 0) ? opts->kc_factor : 1e-2;
+    const int64_t L = b.L;
+    const int n_sel = b.n_sel, n_sp = ctx->n_sp;
+    const int lb = (int)((L + 255) / 256);
+    k_place<<<lb, 256, 0, st>>>(L, ctx->d_lam, lam0_nm, b.lnq, b.c, b.f, b.lamcm);
+    k_consts<<<(n_sel * n_sp + 127) / 128, 128, 0, st>>>(n_sel, d_sel, n_sp, ctx->d_sp_el, ctx->d_sp_stage, ctx->n_el,
+                                                           ctx->d_el, pop, ctx->vturb, b.rc, b.spc);
+    k_kappa0<<<dim3(lb, n_sel), 256, 0, st>>>(L, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS,
+                                               ctx->d_lgW, b.lamcm, n_sp, b.rc, b.spc, b.lnS, b.av, b.lnk0);
+    k_median<<<n_sel, 1024, 0, st>>>(L, b.lnk0, (float)log(kcf), (float)log(cut), b.ln_tp, kc_out);
+    k_prep<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc, b.lnS, b.av,
+                                              b.lnk0, b.ln_tp, b.nb, b.po);
+    k_scan<<<n_sel, 32 * 8, 0, st>>>(b.nb, b.blkcnt, b.classbase, b.classcnt, b.wpart, (long long*)evals);
+    k_scatter<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx, b.bkey);
+    return ranges_launch(b, b.tile, b.cum, st);
+}
+
+int ranges_launch(const PrepBufs& b, int tile, int* cum, cudaStream_t st) {
+    const int nT = (b.N + tile - 1) / tile;
+    const int64_t nr = (int64_t)b.n_sel * kNumClasses * (nT + 3);
+    k_ranges<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(b.n_sel, b.L, nT, tile, b.bkey, b.classbase, b.classcnt,
+                                                          cum);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
+
+TileArgs tile_args(const PrepBufs& b, float* kappa) {
+    TileArgs ta;
+    ta.N = b.N;
+    ta.nT = b.nT;
+    ta.L = b.L;
+    ta.lnq = (float)b.lnq;
+    ta.q1 = (float)(-b.lnq / 2.0);
+    ta.q2 = (float)(b.lnq * b.lnq / 6.0);
+    ta.q3 = (float)(-b.lnq * b.lnq * b.lnq / 24.0);
+    ta.cum = b.cum;
+    ta.bidx = b.bidx;
+    ta.c = b.po.c;
+    ta.f = b.po.f;
+    ta.srel = b.po.srel;
+    ta.a = b.po.a;
+    ta.kv = b.po.kv;
+    ta.jlo = b.po.jlo;
+    ta.jhi = b.po.jhi;
+    ta.ilo = b.po.ilo;
+    ta.ihi = b.po.ihi;
+    ta.ln_tp = b.ln_tp;
+    ta.out = kappa;
+    return ta;
+}
+
+int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
+               float* kappa, float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st) {
     const int prec = opts ? opts->precision : 0;
     if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE)
         return fail(MPSA_EINVAL, "synth: precision %d", prec);
-    const int64_t L = ctx->L;
-    const int n_sp = ctx->n_sp;
-    const double lnq = log1p(1.0 / R);
-    const int nT = (N + kTile - 1) / kTile;
-    const int nb = (int)((L + 255) / 256);
     Scratch sc(st);
-    int *c, *bidx, *bkey, *blkcnt, *classbase, *classcnt, *cum;
-    float *f, *lamcm, *lnS, *av, *lnk0, *ln_tp;
-    RowConst* rc;
-    SpConst* spc;
-    long long* wpart;
-    PrepOut po;
+    PrepBufs b;
     int r;
-    const size_t SL = (size_t)n_sel * L;
-    if ((r = sc.alloc(&c, L)) || (r = sc.alloc(&f, L)) || (r = sc.alloc(&lamcm, L)) ||
-        (r = sc.alloc(&rc, n_sel)) || (r = sc.alloc(&spc, (size_t)n_sel * n_sp)) || (r = sc.alloc(&lnS, SL)) ||
-        (r = sc.alloc(&av, SL)) || (r = sc.alloc(&lnk0, SL)) || (r = sc.alloc(&ln_tp, n_sel)) ||
-        (r = sc.alloc(&po.c, SL)) || (r = sc.alloc(&po.f, SL)) || (r = sc.alloc(&po.srel, SL)) ||
-        (r = sc.alloc(&po.a, SL)) || (r = sc.alloc(&po.kv, SL)) || (r = sc.alloc(&po.jlo, SL)) ||
-        (r = sc.alloc(&po.jhi, SL)) || (r = sc.alloc(&po.ilo, SL)) || (r = sc.alloc(&po.ihi, SL)) ||
-        (r = sc.alloc(&po.cls, SL)) || (r = sc.alloc(&blkcnt, (size_t)n_sel * kNumClasses * nb)) ||
-        (r = sc.alloc(&wpart, (size_t)n_sel * nb)) || (r = sc.alloc(&classbase, (size_t)n_sel * kNumClasses)) ||
-        (r = sc.alloc(&classcnt, (size_t)n_sel * kNumClasses)) || (r = sc.alloc(&bidx, SL)) ||
-        (r = sc.alloc(&bkey, SL)) || (r = sc.alloc(&cum, (size_t)n_sel * kNumClasses * (nT + 3))))
-        return r;
-    po.blkcnt = blkcnt;
-    po.wpart = wpart;
-
-    const int lb = (int)((L + 255) / 256);
-    k_place<<<lb, 256, 0, st>>>(L, ctx->d_lam, lam0_nm, lnq, c, f, lamcm);
-    k_consts<<<(n_sel * n_sp + 127) / 128, 128, 0, st>>>(n_sel, d_sel, n_sp, ctx->d_sp_el, ctx->d_sp_stage,
-                                                           ctx->n_el, ctx->d_el, pop, ctx->vturb, rc, spc);
-    k_kappa0<<<dim3(lb, n_sel), 256, 0, st>>>(L, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS,
-                                               ctx->d_lgW, lamcm, n_sp, rc, spc, lnS, av, lnk0);
-    k_median<<<n_sel, 1024, 0, st>>>(L, lnk0, (float)log(kcf), (float)log(cut), ln_tp, kc_out);
-    k_prep<<<dim3(nb, n_sel), 256, 0, st>>>(L, N, (float)lnq, ctx->d_species, c, f, n_sp, spc, lnS, av, lnk0,
-                                            ln_tp, nb, po);
-    k_scan<<<n_sel, 32 * 8, 0, st>>>(nb, blkcnt, classbase, classcnt, wpart, (long long*)evals);
-    k_scatter<<<dim3(nb, n_sel), 256, 0, st>>>(L, N, po.cls, c, blkcnt, classbase, nb, bidx, bkey);
-    const int64_t nr = (int64_t)n_sel * kNumClasses * (nT + 3);
-    k_ranges<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(n_sel, L, nT, bkey, classbase, classcnt, cum);
-    TileArgs ta;
-    ta.N = N;
-    ta.nT = nT;
-    ta.L = L;
-    ta.lnq = (float)lnq;
-    ta.q1 = (float)(-lnq / 2.0);
-    ta.q2 = (float)(lnq * lnq / 6.0);
-    ta.q3 = (float)(-lnq * lnq * lnq / 24.0);
-    ta.cum = cum;
-    ta.bidx = bidx;
-    ta.c = po.c;
-    ta.f = po.f;
-    ta.srel = po.srel;
-    ta.a = po.a;
-    ta.kv = po.kv;
-    ta.jlo = po.jlo;
-    ta.jhi = po.jhi;
-    ta.ilo = po.ilo;
-    ta.ihi = po.ihi;
-    ta.ln_tp = ln_tp;
-    ta.out = kappa;
+    if ((r = prep_alloc(b, ctx, n_sel, N, R, kTile, [&](auto** p, size_t n) { return sc.alloc(p, n); }))) return r;
+    if ((r = prep_launch(b, ctx, pop, d_sel, lam0_nm, kc_out, evals, opts, st))) return r;
+    const TileArgs ta = tile_args(b, kappa);
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);
-    if (prec == MPSA_PREC_FP32_NAIVE) k_tiles<MPSA_PREC_FP32_NAIVE><<<dim3(nT, n_sel), kTileThreads, 0, st>>>(ta);
-    else k_tiles<MPSA_PREC_FP32_COMPENSATED><<<dim3(nT, n_sel), kTileThreads, 0, st>>>(ta);
+    if (prec == MPSA_PREC_FP32_NAIVE) k_tiles<MPSA_PREC_FP32_NAIVE><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
+    else k_tiles<MPSA_PREC_FP32_COMPENSATED><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
@@ -777,3 +912,375 @@ extern "C" int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_se
     }
     return r;
 }
+
+// ===========================================================================
+// Batched form: many rows on several grids in one persistent, graph-captured launch.
+//
+// At creation every group's line preparation runs once; an autotuner times the
+// persistent profile kernel for each candidate (points per thread, threads per CTA,
+// CTAs per SM) on a sample of tiles and keeps the fastest per grid point; the
+// (row, tile) work units are ordered by decreasing estimated cost (candidate lines
+// per tile, largest first); then the whole pipeline (preparation of every group,
+// one persistent profile launch over all units, the ODFs) is captured into a CUDA
+// graph that mpsa_batch_run replays.
+namespace mpsa {
+namespace {
+
+struct TuneCfg {
+    int pts, threads, minb;
+};
+constexpr TuneCfg kCfgs[] = {{8, 256, 3}, {4, 256, 4}, {8, 128, 6}, {16, 128, 2}};
+constexpr int kNumCfgs = sizeof(kCfgs) / sizeof(kCfgs[0]);
+
+template <int PREC, int PTS, int THREADS, int MINB>
+int persistent_launch_t(const RowDesc* rows, const int2* units, int n_units, int* counter, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    MPSA_CUDA_TRY(cudaGetDevice(&dev));
+    MPSA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MPSA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tiles_persistent<PREC, PTS, THREADS, MINB>,
+                                                                THREADS, 0));
+    const int grid = std::max(1, std::min(n_units, sms * std::max(per_sm, 1)));
+    k_tiles_persistent<PREC, PTS, THREADS, MINB><<<grid, THREADS, 0, st>>>(rows, units, n_units, counter);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
+
+int persistent_launch(int cfg, int prec, const RowDesc* rows, const int2* units, int n_units, int* counter,
+                      cudaStream_t st) {
+    MPSA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    if (prec == MPSA_PREC_FP32_NAIVE) {
+        switch (cfg) {
+            case 0: return persistent_launch_t<1, 8, 256, 3>(rows, units, n_units, counter, st);
+            case 1: return persistent_launch_t<1, 4, 256, 4>(rows, units, n_units, counter, st);
+            case 2: return persistent_launch_t<1, 8, 128, 6>(rows, units, n_units, counter, st);
+            default: return persistent_launch_t<1, 16, 128, 2>(rows, units, n_units, counter, st);
+        }
+    }
+    switch (cfg) {
+        case 0: return persistent_launch_t<0, 8, 256, 3>(rows, units, n_units, counter, st);
+        case 1: return persistent_launch_t<0, 4, 256, 4>(rows, units, n_units, counter, st);
+        case 2: return persistent_launch_t<0, 8, 128, 6>(rows, units, n_units, counter, st);
+        default: return persistent_launch_t<0, 16, 128, 2>(rows, units, n_units, counter, st);
+    }
+}
+
+// Estimated cost of a (row, tile) unit: the number of candidate lines of the tile.
+__global__ void k_unit_cost(const RowDesc* __restrict__ rows, const int2* __restrict__ units, int n_units,
+                            long long* __restrict__ cost) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n_units) return;
+    const int2 rt = units[u];
+    const RowDesc r = rows[rt.x];
+    const int TILE = r.tile, J0 = rt.y * TILE;
+    long long n = 0;
+    for (int b = 0; b < kNumClasses; ++b) {
+        const int reach = 1 << b;
+        int tlo = max(floordiv(J0 - reach + 1, TILE), -1), thi = min(floordiv(J0 + TILE - 1 + reach - 1, TILE), r.nT);
+        if (tlo > thi) continue;
+        const int* cum = r.cum + (size_t)b * (r.nT + 3);
+        n += cum[thi + 2] - cum[tlo + 1];
+    }
+    cost[u] = n;
+}
+
+}  // namespace
+}  // namespace mpsa
+
+struct mpsa_batch {
+    mpsa_ctx* ctx = nullptr;
+    mpsa_synth_opts opts{};
+    int prec = 0, cfg = 0;
+    struct Group {
+        mpsa_lgrid grid{};
+        int N = 0, n_sel = 0;
+        int* d_sel = nullptr;
+        float *kappa = nullptr, *kc = nullptr;
+        int64_t* evals = nullptr;
+        mpsa::PrepBufs pb;
+        int* cum = nullptr;   // tile ranges for the chosen tile size
+        int K = 0, n_steps = 0;
+        int64_t* d_bounds = nullptr;
+        double *d_cw = nullptr, *d_w = nullptr, *odf = nullptr;
+    };
+    std::vector<Group> groups;
+    mpsa::RowDesc* d_rows = nullptr;
+    int n_rows = 0;
+    int2* d_units = nullptr;
+    int n_units = 0;
+    int* d_counter = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> allocs;
+    double tune_ms_per_mpt[mpsa::kNumCfgs] = {0};
+    int n_tuned = 0;
+};
+
+namespace mpsa {
+namespace {
+
+template <class T>
+int balloc(mpsa_batch* b, T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MPSA_ENOMEM, "mpsa_batch_create: cudaMalloc(%zu): %s", n * sizeof(T), cudaGetErrorString(e));
+    }
+    b->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return MPSA_OK;
+}
+
+// Row descriptors for every row of every group with the tile ranges `cums[g]` of tile size `tile`.
+std::vector<RowDesc> row_descs(mpsa_batch* b, int tile, const std::vector<int*>& cums) {
+    std::vector<RowDesc> rows;
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        auto& G = b->groups[g];
+        const int nT = (G.N + tile - 1) / tile;
+        for (int s = 0; s < G.n_sel; ++s) {
+            TileArgs ta = tile_args(G.pb, G.kappa);
+            ta.nT = nT;
+            ta.cum = cums[g];
+            RowDesc r;
+            const size_t sL = (size_t)s * G.pb.L;
+            r.N = G.N;
+            r.nT = nT;
+            r.tile = tile;
+            r.lnq = ta.lnq;
+            r.q1 = ta.q1;
+            r.q2 = ta.q2;
+            r.q3 = ta.q3;
+            r.ln_tp = G.pb.ln_tp + s;
+            r.cum = cums[g] + (size_t)s * kNumClasses * (nT + 3);
+            r.bidx = G.pb.bidx + sL;
+            r.c = G.pb.po.c + sL;
+            r.f = G.pb.po.f + sL;
+            r.srel = G.pb.po.srel + sL;
+            r.a = G.pb.po.a + sL;
+            r.kv = G.pb.po.kv + sL;
+            r.jlo = G.pb.po.jlo + sL;
+            r.jhi = G.pb.po.jhi + sL;
+            r.ilo = G.pb.po.ilo + sL;
+            r.ihi = G.pb.po.ihi + sL;
+            r.out = G.kappa + (size_t)s * G.N;
+            rows.push_back(r);
+        }
+    }
+    return rows;
+}
+
+int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int autotune, cudaStream_t st) {
+    mpsa_ctx* c = b->ctx;
+    int r;
+    // ---- groups: grids, rows, persistent prep buffers, ODF parameters
+    for (int g = 0; g < n_groups; ++g) {
+        const mpsa_batch_group& q = gin[g];
+        mpsa_batch::Group G;
+        G.grid = q.grid;
+        if ((r = check_grid(&q.grid, &G.N))) return r;
+        if (q.n_sel < 1 || !q.sel || !q.kappa_out) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d rows/outputs", g);
+        const int rows = c->n_comp * c->n_points;
+        for (int i = 0; i < q.n_sel; ++i)
+            if (q.sel[i] < 0 || q.sel[i] >= rows) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d sel[%d]", g, i);
+        if ((size_t)q.n_sel * c->L >= (size_t)1 << 31) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d too large", g);
+        G.n_sel = q.n_sel;
+        G.kappa = q.kappa_out;
+        G.kc = q.kappa_c_out;
+        G.evals = q.evals_out;
+        if ((r = balloc(b, &G.d_sel, q.n_sel))) return r;
+        MPSA_CUDA_TRY(cudaMemcpy(G.d_sel, q.sel, q.n_sel * sizeof(int), cudaMemcpyHostToDevice));
+        if ((r = prep_alloc(G.pb, c, q.n_sel, G.N, q.grid.R, kTile, [&](auto** p, size_t n) { return balloc(b, p, n); })))
+            return r;
+        if (q.K > 0) {
+            if (!q.bounds || !q.widths || !q.odf_out) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d ODF args", g);
+            std::vector<double> cw(q.n_steps >= 1 && q.n_steps <= 32 ? q.n_steps + 1 : 1);
+            if ((r = odf_check(q.n_sel, G.N, q.K, q.bounds, q.n_steps, q.widths, MPSA_MEAN_ARITH, cw.data()))) return r;
+            G.K = q.K;
+            G.n_steps = q.n_steps;
+            G.odf = q.odf_out;
+            if ((r = balloc(b, &G.d_bounds, q.K + 1)) || (r = balloc(b, &G.d_cw, q.n_steps + 1)) ||
+                (r = balloc(b, &G.d_w, q.n_steps)))
+                return r;
+            MPSA_CUDA_TRY(cudaMemcpy(G.d_bounds, q.bounds, (q.K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+            MPSA_CUDA_TRY(cudaMemcpy(G.d_cw, cw.data(), (q.n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice));
+            MPSA_CUDA_TRY(cudaMemcpy(G.d_w, q.widths, q.n_steps * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        b->groups.push_back(G);
+        b->n_rows += q.n_sel;
+    }
+    for (auto& G : b->groups)
+        if ((r = prep_launch(G.pb, c, c->d_pop, G.d_sel, G.grid.lambda0_nm, G.kc, G.evals, &b->opts, st))) return r;
+    MPSA_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((r = balloc(b, &b->d_rows, b->n_rows)) || (r = balloc(b, &b->d_counter, 1))) return r;
+
+    // ---- autotune: time per grid point of each configuration on a sample of tiles
+    b->cfg = 0;
+    if (autotune) {
+        cudaEvent_t e0, e1;
+        MPSA_CUDA_TRY(cudaEventCreate(&e0));
+        MPSA_CUDA_TRY(cudaEventCreate(&e1));
+        double best = 1e300;
+        for (int k = 0; k < kNumCfgs; ++k) {
+            const int tile = kCfgs[k].pts * kCfgs[k].threads;
+            std::vector<int*> cums;
+            for (auto& G : b->groups) {
+                const int nT = (G.N + tile - 1) / tile;
+                int* cum;
+                if ((r = balloc(b, &cum, (size_t)G.n_sel * kNumClasses * (nT + 3)))) return r;
+                if ((r = ranges_launch(G.pb, tile, cum, st))) return r;
+                cums.push_back(cum);
+            }
+            std::vector<RowDesc> rows = row_descs(b, tile, cums);
+            // sample: the tiles holding 16 fixed fractions of every row's grid
+            std::vector<int2> units;
+            for (int i = 0; i < (int)rows.size(); ++i)
+                for (int q = 0; q < 16; ++q) {
+                    const int j = (int)((q + 0.5) / 16.0 * rows[i].N);
+                    units.push_back(make_int2(i, j / tile));
+                }
+            int2* du;
+            if ((r = balloc(b, &du, units.size()))) return r;
+            MPSA_CUDA_TRY(cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(RowDesc), cudaMemcpyHostToDevice));
+            MPSA_CUDA_TRY(cudaMemcpy(du, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                MPSA_CUDA_TRY(cudaEventRecord(e0, st));
+                if ((r = persistent_launch(k, b->prec, b->d_rows, du, (int)units.size(), b->d_counter, st))) return r;
+                MPSA_CUDA_TRY(cudaEventRecord(e1, st));
+                MPSA_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                MPSA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                ms_best = std::min(ms_best, ms);
+            }
+            const double per_mpt = ms_best / ((double)units.size() * tile / 1e6);
+            b->tune_ms_per_mpt[k] = per_mpt;
+            if (per_mpt < best) {
+                best = per_mpt;
+                b->cfg = k;
+            }
+        }
+        b->n_tuned = kNumCfgs;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+
+    // ---- final tile ranges, row descriptors and the cost-ordered work list
+    const int tile = kCfgs[b->cfg].pts * kCfgs[b->cfg].threads;
+    std::vector<int*> cums;
+    for (auto& G : b->groups) {
+        const int nT = (G.N + tile - 1) / tile;
+        if ((r = balloc(b, &G.cum, (size_t)G.n_sel * kNumClasses * (nT + 3)))) return r;
+        if ((r = ranges_launch(G.pb, tile, G.cum, st))) return r;
+        cums.push_back(G.cum);
+    }
+    std::vector<RowDesc> rows = row_descs(b, tile, cums);
+    MPSA_CUDA_TRY(cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(RowDesc), cudaMemcpyHostToDevice));
+    std::vector<int2> units;
+    for (int i = 0; i < (int)rows.size(); ++i)
+        for (int t = 0; t < rows[i].nT; ++t) units.push_back(make_int2(i, t));
+    b->n_units = (int)units.size();
+    if ((r = balloc(b, &b->d_units, units.size()))) return r;
+    long long* dcost;
+    if ((r = balloc(b, &dcost, units.size()))) return r;
+    MPSA_CUDA_TRY(cudaMemcpy(b->d_units, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    MPSA_CUDA_TRY(cudaStreamSynchronize(st));
+    k_unit_cost<<<(b->n_units + 255) / 256, 256, 0, st>>>(b->d_rows, b->d_units, b->n_units, dcost);
+    MPSA_CUDA_TRY(cudaGetLastError());
+    std::vector<long long> cost(units.size());
+    MPSA_CUDA_TRY(cudaMemcpyAsync(cost.data(), dcost, cost.size() * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    MPSA_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int> order(units.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<int2> sorted(units.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = units[order[i]];
+    MPSA_CUDA_TRY(cudaMemcpy(b->d_units, sorted.data(), sorted.size() * sizeof(int2), cudaMemcpyHostToDevice));
+
+    // ---- capture the pipeline into a CUDA graph
+    if ((r = odf_setup())) return r;
+    cudaStream_t cap;
+    MPSA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return fail(MPSA_ECUDA, "mpsa_batch_create: begin capture: %s", cudaGetErrorString(e));
+    }
+    int rc = MPSA_OK;
+    for (auto& G : b->groups) {
+        if ((rc = prep_launch(G.pb, c, c->d_pop, G.d_sel, G.grid.lambda0_nm, G.kc, G.evals, &b->opts, cap))) break;
+        if ((rc = ranges_launch(G.pb, tile, G.cum, cap))) break;
+    }
+    if (rc == MPSA_OK) rc = persistent_launch(b->cfg, b->prec, b->d_rows, b->d_units, b->n_units, b->d_counter, cap);
+    if (rc == MPSA_OK)
+        for (auto& G : b->groups)
+            if (G.K > 0 && (rc = odf_launch(G.kappa, G.n_sel, G.N, G.K, G.d_bounds, G.n_steps, G.d_cw, G.d_w, G.odf, cap)))
+                break;
+    e = cudaStreamEndCapture(cap, &b->graph);
+    cudaStreamDestroy(cap);
+    if (rc != MPSA_OK) return rc;
+    if (e != cudaSuccess) return fail(MPSA_ECUDA, "mpsa_batch_create: end capture: %s", cudaGetErrorString(e));
+    MPSA_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return MPSA_OK;
+}
+
+}  // namespace
+}  // namespace mpsa
+
+extern "C" {
+
+int mpsa_batch_create(mpsa_ctx* ctx, int32_t n_groups, const mpsa_batch_group* groups, const mpsa_synth_opts* opts,
+                      int32_t autotune, void* stream, mpsa_batch** out) {
+    if (!ctx || !groups || !out || n_groups < 1) return fail(MPSA_EINVAL, "mpsa_batch_create: bad argument");
+    if (ctx->L < 1 || !ctx->d_pop) return fail(MPSA_ESTATE, "mpsa_batch_create: load a line list and a grid first");
+    for (int i = 0; i < ctx->n_sp; ++i)
+        if (ctx->h_sp_el[i] >= ctx->n_el) return fail(MPSA_EINVAL, "mpsa_batch_create: species/element mismatch");
+    const int prec = opts ? opts->precision : 0;
+    if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE)
+        return fail(MPSA_EINVAL, "mpsa_batch_create: precision %d", prec);
+    MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
+    *out = nullptr;
+    mpsa_batch* b = new mpsa_batch();
+    b->ctx = ctx;
+    if (opts) b->opts = *opts;
+    b->prec = prec;
+    const int r = batch_build(b, groups, n_groups, autotune, (cudaStream_t)stream);
+    if (r != MPSA_OK) {
+        mpsa_batch_destroy(b);
+        return r;
+    }
+    *out = b;
+    return MPSA_OK;
+}
+
+int mpsa_batch_run(mpsa_batch* b, void* stream) {
+    if (!b || !b->exec) return fail(MPSA_EINVAL, "mpsa_batch_run: bad batch");
+    MPSA_CUDA_TRY(cudaSetDevice(b->ctx->device));
+    prof_mark(b->ctx, MPSA_KERNEL_PROFILE, (cudaStream_t)stream);
+    MPSA_CUDA_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    prof_mark(b->ctx, MPSA_KERNEL_PROFILE, (cudaStream_t)stream);
+    return MPSA_OK;
+}
+
+int mpsa_batch_get_info(const mpsa_batch* b, mpsa_batch_info* out) {
+    if (!b || !out) return fail(MPSA_EINVAL, "mpsa_batch_get_info: bad argument");
+    out->pts_per_thread = kCfgs[b->cfg].pts;
+    out->threads = kCfgs[b->cfg].threads;
+    out->min_blocks = kCfgs[b->cfg].minb;
+    out->n_rows = b->n_rows;
+    out->n_units = b->n_units;
+    out->n_tuned = b->n_tuned;
+    for (int k = 0; k < 8; ++k) out->tune_ms_per_mpoint[k] = k < kNumCfgs ? b->tune_ms_per_mpt[k] : 0.0;
+    return MPSA_OK;
+}
+
+void mpsa_batch_destroy(mpsa_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+}  // extern "C"

@@ -51,9 +51,20 @@ def test_adversarial():
     cases = [np.zeros(n), np.full(n, 3.5), np.r_[np.zeros(n - 1), 1e30], np.repeat([1.0, 2.0, 3.0], [2000, 1, 2999]),
              np.r_[np.zeros(n // 2), np.ones(n - n // 2)], rng.integers(0, 3, n).astype(float),
              np.r_[1e-40 * np.ones(100), rng.lognormal(0, 1, n - 100)],          # denormals
-             rng.lognormal(-80, 10, n)]                                          # very small and wide
+             rng.lognormal(-80, 10, n),                                          # very small and wide
+             1.0 + 1e-2 * rng.random(n),                                         # narrow: 1 % spread
+             1.0 + 1e-6 * rng.random(n),                                         # a few ulps apart
+             np.r_[np.zeros(3000), 1.0 + 1e-3 * rng.random(n - 3000)]]           # zeros + narrow
     for x in cases:
         check(x, [0, n], W12)
+
+
+def test_narrow_large_intervals():
+    # smooth, narrow opacity over long intervals (the far-wing dominated rows of the table)
+    rng = np.random.default_rng(5)
+    n = 120_000
+    x = 1e3 * (1.0 + 0.05 * np.sin(np.linspace(0, 40, n)) + 1e-4 * rng.random(n))
+    check(x, wl.equal_intervals(n, 3), W12)
 
 
 def test_small_and_ragged_intervals():
