@@ -52,8 +52,11 @@ def parse():
     p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank (table workload)")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
-    p.add_argument("--mode", choices=["step", "serve"], default="step",
-                   help="step: the throughput benchmark; serve: Poisson request stream through the server")
+    p.add_argument("--mode", choices=["step", "serve", "batch"], default="step",
+                   help="step: the throughput benchmark; serve: Poisson request stream through the server; "
+                        "batch: persistent graph-captured batch against the plain per-point path")
+    p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
+    p.add_argument("--batch-windows", type=int, default=24, help="spectrum windows in the batch sample")
     p.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of the request stream")
     p.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
     p.add_argument("--serve-limit", type=float, default=90.0, help="wall-clock limit of a serving run [s]")
@@ -216,19 +219,13 @@ def native_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2105_13611_gb300.sharding import reduce_scalar
+
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_scalar(x, "max")
 
     def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_scalar(x, "sum")
 
     w = wl.config_table() if args.workload == "table" else wl.config_small()
     lines = w.lines()
@@ -474,8 +471,96 @@ def serve_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def batch_arm(args):
+    """64 compositions x 1425 (T, P) rows plus spectrum windows (1-500 nm at R = 5e5): a seeded
+    sample of ODF rows and windows runs (a) point by point through synth_opacity / build_odf and
+    (b) as one persistent graph-captured batch; same results, compared throughput."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    ab = wl.abundance_scales(64, el.n, seed=77)
+    ctx = binding.Context(0)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P, abund_scale=ab)
+    nrows = 64 * len(w.T)
+    rng = np.random.default_rng(99)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    bounds = wl.equal_intervals(N, w.n_intervals)
+    groups = []
+    odf_rows = rng.choice(nrows, args.batch_rows, replace=False).astype(np.int32)
+    groups.append(dict(grid=w.grid, sel=odf_rows, bounds=bounds, widths=w.widths, odf_on=True))
+    for _ in range(args.batch_windows):
+        L = float(np.exp(rng.uniform(0.0, math.log(500.0))))
+        lam0 = float(rng.uniform(9.0, 10000.0 - L))
+        groups.append(dict(grid=wl.Grid(lam0, lam0 + L, 5e5), sel=np.array([rng.integers(0, nrows)], dtype=np.int32),
+                           odf_on=False))
+    for g in groups:
+        n = binding.grid_size(g["grid"].lam0_nm, g["grid"].lam1_nm, g["grid"].R)
+        g["kappa"] = torch.empty((len(g["sel"]), n), dtype=torch.float32, device="cuda")
+        g["kappa_c"] = torch.empty(len(g["sel"]), dtype=torch.float32, device="cuda")
+        g["evals"] = torch.empty(len(g["sel"]), dtype=torch.int64, device="cuda")
+        if g["odf_on"]:
+            g["odf"] = torch.empty((len(g["sel"]), w.n_intervals, 12), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    # (a) plain per-point path
+    plain_out = []
+
+    def plain():
+        outs = []
+        for g in groups:
+            for i, r in enumerate(g["sel"]):
+                k = g["kappa"][i:i + 1]
+                ctx.synth_opacity(g["grid"], [int(r)], k, g["kappa_c"][i:i + 1], g["evals"][i:i + 1], stream=st)
+                if g["odf_on"]:
+                    ctx.build_odf(k, g["bounds"], g["widths"], g["odf"][i:i + 1], stream=st)
+        return outs
+
+    plain()
+    torch.cuda.synchronize()
+    evals = int(sum(int(g["evals"].sum()) for g in groups))
+    ref = [(g["kappa"].clone(), g.get("odf").clone() if g["odf_on"] else None) for g in groups]
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plain()
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / args.steps
+    # (b) batched
+    t0 = time.perf_counter()
+    batch = binding.Batch(ctx, groups, autotune=True)
+    t_create = time.perf_counter() - t0
+    batch.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        batch.run(stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
+    worst = 0.0
+    for g, (k_ref, o_ref) in zip(groups, ref):
+        kb, kr = g["kappa"].double(), k_ref.double()
+        kc = g["kappa_c"].double()[:, None]
+        worst = max(worst, float(((kb - kr).abs() / (kr + kc)).max()))
+    info = batch.info()
+    batch.close()
+    out = {"mode": "batch", "metric": "line-evals/s, persistent graph-captured batch vs plain per-point path",
+           "rows": {"odf_rows": len(odf_rows), "windows": args.batch_windows, "compositions": 64},
+           "evals_per_run": evals, "plain_s": t_plain, "batch_s": t_batch,
+           "plain_evals_per_s": evals / t_plain, "batch_evals_per_s": evals / t_batch, "speedup": t_plain / t_batch,
+           "batch_create_s": t_create, "max_rel_diff_vs_plain": worst, "autotune": info, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        batch_arm(args)
+        return
     if args.mode == "serve":
         serve_arm(args)
         return
