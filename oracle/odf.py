@@ -51,6 +51,33 @@ def step_means_sorted(xs: np.ndarray, widths) -> np.ndarray:
     return out
 
 
+def geom_step_means_sorted(xs: np.ndarray, widths) -> np.ndarray:
+    """Geometric step means exp((1/w_s) integral ln x(u) du) of sorted non-negative values.
+
+    A step whose rank range overlaps the zero values (with positive length) has geometric
+    mean 0 (the geometric mean of a set containing 0); otherwise the integral runs over
+    positive values only.
+    """
+    n = len(xs)
+    z = int(np.count_nonzero(xs == 0))
+    c = cumulative_widths(widths)
+    w = np.asarray(widths, dtype=np.float64)
+    lx = np.log(xs[z:].astype(np.float64))
+    pref = np.concatenate([[0.0], np.cumsum(lx)])
+
+    def F(u):  # integral of ln x over ranks [z, u) for u >= z
+        k = int(math.floor(u))
+        if k >= n:
+            return pref[n - z]
+        return pref[k - z] + (u - k) * float(lx[k - z])
+
+    out = np.empty(len(w))
+    for s in range(len(w)):
+        a, b = c[s] * n, c[s + 1] * n
+        out[s] = 0.0 if a < z else math.exp((F(b) - F(a)) / (w[s] * n))
+    return out
+
+
 def odf(kappa: np.ndarray, bounds, widths, mean: str = "arith") -> np.ndarray:
     """ODF table of one opacity array: [K][n_steps] FP64.
 
@@ -63,7 +90,7 @@ def odf(kappa: np.ndarray, bounds, widths, mean: str = "arith") -> np.ndarray:
     for k in range(K):
         xs = np.sort(np.asarray(kappa[b[k]:b[k + 1]], dtype=np.float64))
         if mean == "geom":
-            out[k] = np.exp(step_means_sorted(np.log(xs), widths))
+            out[k] = geom_step_means_sorted(xs, widths)
         else:
             out[k] = step_means_sorted(xs, widths)
     return out
