@@ -36,8 +36,9 @@ import workloads as wl  # noqa: E402
 METRIC = "Voigt line-evals/s (line-by-line opacity synthesis + ODF binning)"
 UNIT = "line-evals/s"
 # FP32 operations of one far-wing profile evaluation (the tier that takes > 98% of
-# evaluations): v = fma(G, kvB, kvE1); V-term fma; reciprocal argument; y(2+4y) fma;
-# two multiplies by strength; accumulate: 3 FFMA (6 flop) + 3 FMUL + 1 FADD = 10 flop.
+# evaluations): v' = fma(G, sqrt2 kv B, sqrt2 kv E1); D = fma(v', v', 2a^2 - 1);
+# denominator fma(D, D, 8a^2); numerator fma(2sk, D, 4sk); accumulate fma(num, 1/den, sum):
+# 5 FFMA = 10 flop, plus one reciprocal on the special-function unit (not counted).
 FLOP_PER_EVAL = 10
 SMS = 152
 FP32_LANES_PER_SM = 128
@@ -50,9 +51,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--batch", type=int, default=8, help="(T, P) points per step and rank (table workload)")
+    p.add_argument("--rows", type=str, default="",
+                   help="comma-separated table rows (T index * 25 + P index) instead of the default batch")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
-    p.add_argument("--mode", choices=["step", "serve", "batch"], default="step",
+    p.add_argument("--mode", choices=["step", "serve", "batch", "precision"], default="step",
                    help="step: the throughput benchmark; serve: Poisson request stream through the server; "
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
@@ -237,7 +240,10 @@ def native_arm(args):
     N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
     K = w.n_intervals
     bounds = wl.equal_intervals(N, K)
-    sel = batch_points(rank, args.batch) if args.workload == "table" else np.arange(len(w.T), dtype=np.int32)
+    if args.rows:
+        sel = np.array([int(x) for x in args.rows.split(",")], dtype=np.int32)
+    else:
+        sel = batch_points(rank, args.batch) if args.workload == "table" else np.arange(len(w.T), dtype=np.int32)
     B = len(sel)
     stream = torch.cuda.current_stream()
     kap = torch.empty((B, N), dtype=torch.float32, device=dev)
@@ -374,7 +380,6 @@ def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
     Spectrum: grey atmosphere with D ~ U{40..120} depths, Teff ~ U(3500, 12000) K, log g ~ U(1, 5);
     window length ~ logU(1, 500) nm placed uniformly in 9-10000 nm at R = 5e5; 5 mu angles.
     ODF: one composition x the 57 x 25 T-P grid over 1-10 contiguous intervals of the 328-interval grid."""
-    from oracle import spectrum as spc  # grey-law atmosphere builder only (no synthesis)
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
     while True:
@@ -386,7 +391,7 @@ def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
             Teff, logg = rng.uniform(3500, 12000), rng.uniform(1, 5)
             L = float(np.exp(rng.uniform(math.log(1.0), math.log(500.0))))
             lam0 = float(rng.uniform(9.0, 10000.0 - L))
-            m, T, P = spc.grey_atmosphere(D, Teff, logg)
+            m, T, P = wl.grey_atmosphere(D, Teff, logg)
             out.append((t, "spectrum", (m, T, P, wl.Grid(lam0, lam0 + L, 5e5))))
         else:
             nint = int(rng.integers(1, 11))
@@ -556,8 +561,70 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def precision_arm(args):
+    """Precision study: a 1e8-line list (same distributions, 9-10000 nm) on a 6 x 5 (T, P)
+    subset of the table, synthesised on a 1 nm slice (300-301 nm at R = 2e6, every line of the
+    list whose cut window reaches it) with the four precisions of the library; relative errors
+    of opacity and ODF steps against the all-FP64 GPU variant (itself checked against the FP64
+    oracle by the GPU tests)."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    n_lines = int(os.environ.get("MPSA_PRECISION_LINES", "100000000"))
+    t0 = time.perf_counter()
+    lines = wl.linelist(n_lines, 30, 9.0, 10000.0, seed=1002)
+    t_gen = time.perf_counter() - t0
+    print(f"precision: generated {n_lines} lines in {t_gen:.1f} s", file=sys.stderr, flush=True)
+    el = wl.elements(15)
+    se, ss = wl.species_table(15)
+    T, P = wl.tp_grid_dfsynthe()
+    ti, pi = np.array([4, 14, 24, 34, 44, 54]), np.array([2, 7, 12, 17, 22])
+    rows = (ti[:, None] * 25 + pi[None, :]).reshape(-1).astype(np.int32)
+    ctx = binding.Context(0)
+    t0 = time.perf_counter()
+    ctx.load_linelist(lines, se, ss)
+    t_load = time.perf_counter() - t0
+    print(f"precision: loaded in {t_load:.1f} s", file=sys.stderr, flush=True)
+    ctx.set_atmosphere_grid(el, T, P)
+    g = wl.Grid(300.0, 301.0, 2e6)
+    N = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
+    b = wl.equal_intervals(N, 4)
+    res, times, evals = {}, {}, None
+    names = {2: "fp64_all", 1: "fp32_naive_sums", 0: "fp32_kahan_sums", 3: "fp32_kahan_fp32_populations"}
+    for prec in (2, 1, 0, 3):
+        k = torch.empty((len(rows), N), dtype=torch.float32, device="cuda")
+        kc = torch.empty(len(rows), dtype=torch.float32, device="cuda")
+        ev = torch.empty(len(rows), dtype=torch.int64, device="cuda")
+        o = torch.empty((len(rows), 4, 12), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(rows)):       # one row per call: scratch is ~57 B per (row, line)
+            ctx.synth_opacity(g, rows[i:i + 1], k[i:i + 1], kc[i:i + 1], ev[i:i + 1],
+                              opts=binding.make_opts(1e-3, 1e-2, prec))
+        ctx.build_odf(k, b, wl.ODF_WIDTHS_12, o)
+        torch.cuda.synchronize()
+        times[names[prec]] = time.perf_counter() - t0
+        print(f"precision: {names[prec]} {times[names[prec]]:.1f} s", file=sys.stderr, flush=True)
+        res[prec] = (k.double().cpu().numpy(), kc.double().cpu().numpy(), o.cpu().numpy())
+        evals = int(ev.sum())
+    kr, kcr, orf = res[2]
+    out = {"mode": "precision", "lines": n_lines, "rows": "6 T x 5 P of the 57 x 25 grid", "slice_nm": [300.0, 301.0],
+           "grid_points": N, "evals_per_variant": evals, "reference": "fp64_all (GPU)",
+           "generate_s": t_gen, "load_s": t_load, "seconds": times, "variants": {}}
+    for prec in (1, 0, 3):
+        k, kc, o = res[prec]
+        rel = np.abs(k - kr) / (kr + kcr[:, None])
+        ro = np.abs(o - orf) / np.maximum(np.abs(orf), 1e-300)
+        out["variants"][names[prec]] = {"opacity_max_rel": float(rel.max()), "opacity_p99_rel": float(np.quantile(rel, 0.99)),
+                                        "odf_max_rel": float(ro.max()), "odf_p99_rel": float(np.quantile(ro, 0.99))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "precision":
+        precision_arm(args)
+        return
     if args.mode == "batch":
         batch_arm(args)
         return

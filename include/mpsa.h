@@ -94,6 +94,10 @@ typedef struct {
 
 #define MPSA_PREC_FP32_COMPENSATED 0   /* FP32 profiles, chunked FP32 partials + Kahan fold */
 #define MPSA_PREC_FP32_NAIVE       1   /* FP32 profiles, plain FP32 running sums            */
+#define MPSA_PREC_FP64             2   /* FP64 line terms, profiles and sums (precision study;
+                                          FP64 runs far below the FP32 rate on this GPU)     */
+#define MPSA_PREC_FP32_POP32       3   /* as 0, with the population table rounded to FP32
+                                          before the line terms (precision study)            */
 
 /*
  * load_linelist -- copy a line list and its species table into the context.
@@ -169,11 +173,15 @@ int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const in
  *   n_steps, widths[n_steps] (host): sub-bin width fractions, positive, summing
  *     to 1 within 1e-12.  n_steps <= 32.
  *   mean_kind: MPSA_MEAN_ARITH (arithmetic mean of the sub-bin) or
- *     MPSA_MEAN_GEOM (exp of the mean of ln kappa; zero values give 0).
+ *     MPSA_MEAN_GEOM (exp of the sub-bin integral of ln kappa divided by its
+ *     width, the paper's default in Sect. 2.3; a sub-bin whose rank range
+ *     reaches into zero values has geometric mean 0).
  *   odf_out (device, double[n_rows][K][n_steps]).
  * Order statistics are found by a 4-level radix multi-select on the FP32 bit
  * patterns with exact integer partial sums; only the final cross-exponent
- * reduction is FP64.  Stream-ordered, no host synchronisation.
+ * reduction is FP64.  Geometric means take one more pass that sums ln kappa
+ * (exponent in FP64, mantissa by FP32 logf) between consecutive order
+ * statistics in FP64.  Stream-ordered, no host synchronisation.
  * Errors: MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
  */
 int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N,
@@ -256,6 +264,7 @@ typedef struct {
     int32_t n_steps;
     const double* widths;      /* host */
     double* odf_out;           /* device double[n_sel][K][n_steps] */
+    int32_t mean_kind;         /* MPSA_MEAN_ARITH or MPSA_MEAN_GEOM */
 } mpsa_batch_group;
 
 typedef struct {
@@ -299,7 +308,7 @@ typedef struct {
     const double* mu;
     float* I_out;              /* host float[n_mu][N_win], written on completion */
     /* ODF: rows of the atmosphere grid, synthesised on `grid` and reduced with
-       build_odf's rules (arithmetic means); host arrays copied at submit */
+       build_odf's rules; host arrays copied at submit */
     int32_t n_sel;
     const int32_t* sel;
     mpsa_lgrid grid;
@@ -309,6 +318,7 @@ typedef struct {
     const double* widths;
     double* odf_out;           /* host double[n_sel][K][n_steps], written on completion */
     float* kappa_c_out;        /* host float[n_sel] or NULL */
+    int32_t mean_kind;         /* ODF: MPSA_MEAN_ARITH or MPSA_MEAN_GEOM */
 } mpsa_request;
 
 typedef struct {
@@ -348,6 +358,22 @@ void mpsa_server_destroy(mpsa_server* s);
 #define MPSA_KERNEL_ODF     1
 int mpsa_profile_enable(mpsa_ctx* ctx, int enable);
 int mpsa_profile_read(mpsa_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
+
+/*
+ * mpsa_voigt -- the Voigt function H(v, a) = Re w(v + i a) of the line profile
+ * (paper Sect. 2.1: argument v = (nu - nu0)/dnu_D, damping a = gamma/(4 pi dnu_D)),
+ * evaluated on the device exactly as the synthesis kernels evaluate it, for
+ * accuracy tests of the profile tiers.
+ *   v, a (device, double[n]): arguments (a > 0; the sign of v is ignored).
+ *   precision: MPSA_PREC_FP64 evaluates the FP64 tiers in double; any other value
+ *     rounds v and a to FP32 and evaluates the FP32 tiers (far: rational or
+ *     one-level continued fraction; mid: five-level continued fraction; core:
+ *     shifted 12-point Gauss-Hermite).
+ *   out (device, double[n]): H, widened from FP32 for the FP32 tiers.
+ * Stream-ordered.  Errors: MPSA_EINVAL, MPSA_ECUDA.
+ */
+int mpsa_voigt(mpsa_ctx* ctx, const double* v, const double* a, int64_t n, int32_t precision, double* out,
+               void* stream);
 
 #ifdef __cplusplus
 }

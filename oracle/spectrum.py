@@ -32,11 +32,9 @@ def planck_lambda(lam_cm, T):
 
 
 def grey_atmosphere(D: int, Teff: float, logg: float, log_tau_top=-6.8, log_tau_bot=2.0, kappa_bar=0.1):
-    tau = 10.0 ** np.linspace(log_tau_top, log_tau_bot, D)
-    T = Teff * (0.75 * (tau + 2.0 / 3.0)) ** 0.25
-    m = tau / kappa_bar
-    P = 10.0 ** logg * m
-    return m, T, P
+    """The grey model atmosphere of the spectrum workload (an input, from workloads)."""
+    import workloads
+    return workloads.grey_atmosphere(D, Teff, logg, log_tau_top, log_tau_bot, kappa_bar)
 
 
 def optical_depth(kappa, m):

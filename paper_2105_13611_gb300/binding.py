@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("MPSA_LIBRARY") or os.path.join(HERE, "_lib", "libmpsa.so")
 
 MPSA_OK, MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA, MPSA_ESTATE, MPSA_ETIMEOUT = 0, -1, -2, -3, -4, -5
-PREC_FP32_COMPENSATED, PREC_FP32_NAIVE = 0, 1
+PREC_FP32_COMPENSATED, PREC_FP32_NAIVE, PREC_FP64, PREC_FP32_POP32 = 0, 1, 2, 3
 MEAN_ARITH, MEAN_GEOM = 0, 1
 
 EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "mpsa_grid_size",
@@ -23,7 +23,7 @@ EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "m
             "mpsa_profile_enable", "mpsa_profile_read", "build_odf_noalloc",
             "mpsa_server_create", "mpsa_server_submit", "mpsa_server_wait", "mpsa_server_get_stats",
             "mpsa_server_destroy", "mpsa_server_cancel_queued",
-            "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy"]
+            "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy", "mpsa_voigt"]
 REQ_SPECTRUM, REQ_ODF = 1, 2
 KERNEL_PROFILE, KERNEL_ODF = 0, 1
 
@@ -58,13 +58,14 @@ class Request(C.Structure):
     _fields_ = [("kind", C.c_int32), ("atm", Atmos), ("win", LGrid), ("n_mu", C.c_int32), ("mu", _dp),
                 ("I_out", _fp), ("n_sel", C.c_int32), ("sel", _ip), ("grid", LGrid), ("K", C.c_int32),
                 ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", _dp),
-                ("kappa_c_out", _fp)]
+                ("kappa_c_out", _fp), ("mean_kind", C.c_int32)]
 
 
 class BatchGroup(C.Structure):
     _fields_ = [("grid", LGrid), ("n_sel", C.c_int32), ("sel", _ip), ("kappa_out", C.c_void_p),
                 ("kappa_c_out", C.c_void_p), ("evals_out", C.c_void_p), ("K", C.c_int32),
-                ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", C.c_void_p)]
+                ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", C.c_void_p),
+                ("mean_kind", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
@@ -131,6 +132,8 @@ def load_library(path: str = LIB_PATH):
     lib.mpsa_batch_destroy.restype = None
     for f in ("mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info"):
         getattr(lib, f).restype = C.c_int
+    lib.mpsa_voigt.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, vp, vp]
+    lib.mpsa_voigt.restype = C.c_int
     lib.mpsa_profile_enable.argtypes = [vp, C.c_int]
     lib.mpsa_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     for f in ("mpsa_create", "load_linelist", "set_atmosphere_grid", "synth_opacity", "build_odf", "synth_spectrum",
@@ -264,6 +267,11 @@ class Context:
         _check(self.lib.build_odf(self.h, _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
                                   _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream)))
 
+    def voigt(self, v, a, out, precision=0, stream=None):
+        """H(v, a) on the device as the kernels evaluate it; v, a, out: device float64 tensors."""
+        _check(self.lib.mpsa_voigt(self.h, _dev(v), _dev(a), int(v.numel()), int(precision), _dev(out),
+                                   _stream(stream)))
+
     def synth_spectrum(self, m, T, P, win, mus, I_out, comp=0, opts=None, stream=None):
         m = _arr(m, np.float64)
         T = _arr(T, np.float64)
@@ -309,7 +317,7 @@ class Server:
         self._pending[t.value] = (out,)
         return t.value
 
-    def submit_odf(self, sel, grid, bounds, widths):
+    def submit_odf(self, sel, grid, bounds, widths, mean_kind=MEAN_ARITH):
         s = _arr(sel, np.int32); b = _arr(bounds, np.int64); w = _arr(widths, np.float64)
         out = np.empty((len(s), len(b) - 1, len(w)), dtype=np.float64)
         kc = np.empty(len(s), dtype=np.float32)
@@ -324,6 +332,7 @@ class Server:
         q.widths = _ptr(w, C.c_double)
         q.odf_out = _ptr(out, C.c_double)
         q.kappa_c_out = _ptr(kc, C.c_float)
+        q.mean_kind = mean_kind
         t = C.c_int64()
         _check(self.lib.mpsa_server_submit(self.h, C.byref(q), C.byref(t)))
         self._pending[t.value] = (out, kc)
@@ -386,6 +395,7 @@ class Batch:
                 q.n_steps = len(w)
                 q.widths = _ptr(w, C.c_double)
                 q.odf_out = _dev(g["odf"])
+                q.mean_kind = g.get("mean_kind", MEAN_ARITH)
             else:
                 q.K = 0
         o = opts if opts is not None else make_opts()

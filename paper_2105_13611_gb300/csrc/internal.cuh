@@ -18,9 +18,9 @@ int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, do
 int check_grid(const mpsa_lgrid* g, int* N);
 
 // ODF kernel launch on device-resident bounds [K+1], cumulative widths [n_steps+1]
-// and widths [n_steps] (odf.cu).
+// and widths [n_steps]; mean_kind MPSA_MEAN_ARITH or MPSA_MEAN_GEOM (odf.cu).
 int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* d_bounds, int n_steps,
-               const double* d_cw, const double* d_w, double* d_out, cudaStream_t st);
+               const double* d_cw, const double* d_w, double* d_out, int mean_kind, cudaStream_t st);
 
 // One-time kernel attribute set-up of the ODF kernel on the current device (call outside
 // stream capture) (odf.cu).

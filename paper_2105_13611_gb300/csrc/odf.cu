@@ -19,6 +19,12 @@
 // level-1 bin into a shared-memory candidate buffer; levels 2-4 then run on that
 // buffer.  If the candidates do not fit, levels 2-4 re-read the interval instead.
 // Zeros are counted in registers and never enter atomics or the buffer.
+//
+// Geometric means (exp of the same integral of ln x) reuse the order statistics: one
+// more pass (from L2) sums ln x of the positive values between consecutive distinct
+// order statistics in FP64, and
+//   G(u) = sum_{0 < x < theta} ln x + (u - #{x < theta}) ln theta   (u at or above the zeros);
+// a sub-bin that reaches into the zero values has geometric mean 0.
 #include <math.h>
 #include <string.h>
 
@@ -58,6 +64,7 @@ __device__ __forceinline__ unsigned long long group_base(unsigned E) { return E 
 // f(bits, valid), so warp-wide votes inside f are safe.
 template <class F>
 __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long long n, F&& f) {
+    constexpr int U = 4;   // 16-byte loads in flight per thread before any of them is consumed
     const int tid = threadIdx.x;
     const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
     long long head = mis ? (long long)(4u - mis) : 0;
@@ -66,14 +73,21 @@ __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long
     const long long nv = (n - head) >> 2;
     const long long per = (nv + kOdfThreads - 1) / kOdfThreads;
     const long long i0 = (long long)tid * per;
-    for (long long it = 0; it < per; ++it) {
-        const long long i = i0 + it;
-        const bool v = i < nv;
-        const float4 q = v ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        f(__float_as_uint(q.x), v);
-        f(__float_as_uint(q.y), v);
-        f(__float_as_uint(q.z), v);
-        f(__float_as_uint(q.w), v);
+    for (long long it = 0; it < per; it += U) {
+        float4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = i0 + it + u;
+            q[u] = (it + u < per && i < nv) ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool v = (it + u < per) && (i0 + it + u < nv);
+            f(__float_as_uint(q[u].x), v);
+            f(__float_as_uint(q[u].y), v);
+            f(__float_as_uint(q[u].z), v);
+            f(__float_as_uint(q[u].w), v);
+        }
     }
     const long long t0 = head + (nv << 2);
     f(tid < head ? __float_as_uint(__ldg(x + tid)) : 0u, tid < head);
@@ -101,6 +115,44 @@ struct RunAdd {
         val = 0;
     }
 };
+
+// Run merging of FP64 sums into a shared-memory array (geometric pass).
+struct RunAddF64 {
+    int key = -1;
+    double val = 0.0;
+    __device__ __forceinline__ void add(double* __restrict__ h, int k, double v) {
+        if (k == key) {
+            val += v;
+        } else {
+            if (key >= 0) atomicAdd(&h[key], val);
+            key = k;
+            val = v;
+        }
+    }
+    __device__ __forceinline__ void flush(double* __restrict__ h) {
+        if (key >= 0) atomicAdd(&h[key], val);
+        key = -1;
+        val = 0.0;
+    }
+};
+
+// ln x of a positive finite FP32 value given by its bits: x = 2^e m with m in
+// [1/sqrt 2, sqrt 2), ln x = e ln 2 (FP64, exact e) + ln m (FP32 logf, |ln m| < 0.35),
+// so the absolute error stays near 2e-8 whatever the exponent.
+__device__ __forceinline__ double ln_f32_bits(unsigned bits) {
+    int e = 0;
+    if (bits < 0x00800000u) {   // subnormal: scale by 2^23 (exact)
+        bits = __float_as_uint(__uint_as_float(bits) * 8388608.0f);
+        e = -23;
+    }
+    e += (int)(bits >> 23) - 127;
+    unsigned mb = (bits & 0x7fffffu) | 0x3f800000u;
+    if (mb > 0x3fb504f3u) {   // m > sqrt 2: halve it
+        mb -= 0x00800000u;
+        e += 1;
+    }
+    return (double)e * 0.69314718055994530942 + (double)logf(__uint_as_float(mb));
+}
 
 // One warp resolves one target inside its slot's 2^wb-bin histogram h (packed counts and
 // low-bit sums): finds the sub-bin holding rank t.k and adds the counts and exact sums
@@ -159,7 +211,7 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
 __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ kappa, int64_t N, int K,
                                                      const int64_t* __restrict__ bounds, int n_steps,
                                                      const double* __restrict__ cw, const double* __restrict__ w,
-                                                     double* __restrict__ out) {
+                                                     double* __restrict__ out, int geom) {
     extern __shared__ unsigned long long sm[];
     const int nt = n_steps - 1;
     const int nslots = nt > 4 ? nt : 4;
@@ -176,6 +228,9 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     __shared__ int n_distinct, n_cand;
     __shared__ long long s_zero;
     __shared__ int wtot[kOdfWarps];
+    __shared__ unsigned thr[kMaxTargets];       // geometric pass: distinct order statistics, ascending
+    __shared__ double lsum[kMaxTargets + 1];    // geometric pass: inclusive prefix sums of ln x per bucket
+    __shared__ int n_thr;
 
     const int k = blockIdx.x, row = blockIdx.y;
     const int64_t b0 = bounds[k], b1 = bounds[k + 1];
@@ -353,11 +408,20 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             return q;
         };
         if (collect) {
+            // warp-aggregated append: one shared atomic per warp and call
             for_each_value(x, n, [&](unsigned bits, bool valid) {
                 bits &= 0x7fffffffu;
-                if (!valid || slot_of(bits) < 0) return;
-                const int pos = atomicAdd(&n_cand, 1);
-                if (pos < kCand) cand[pos] = bits;
+                const bool take = valid && slot_of(bits) >= 0;
+                const unsigned m = __ballot_sync(0xffffffffu, take);
+                if (m == 0u) return;
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&n_cand, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (take) {
+                    const int pos = base + __popc(m & ((1u << lane) - 1u));
+                    if (pos < kCand) cand[pos] = bits;
+                }
             });
             __syncthreads();
             nc = min(n_cand, kCand);
@@ -395,6 +459,59 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         }
         nd_prev = nd;
         __syncthreads();
+    }
+
+    if (geom) {
+        if (tid == 0) {
+            int m = 0;
+            for (int t = 0; t < nt; ++t) {
+                if (tg[t].total) continue;
+                const unsigned p = tg[t].prefix;
+                bool dup = false;
+                for (int q = 0; q < m; ++q) dup |= thr[q] == p;
+                if (dup) continue;
+                int i = m++;
+                while (i > 0 && thr[i - 1] > p) { thr[i] = thr[i - 1]; --i; }
+                thr[i] = p;
+            }
+            n_thr = m;
+        }
+        for (int i = tid; i <= kMaxTargets; i += kOdfThreads) lsum[i] = 0.0;
+        __syncthreads();
+        const int m = n_thr;
+        // bucket of x = number of order statistics <= x; values below thr[j] sit in buckets 0..j
+        RunAddF64 run;
+        for_each_value(x, n, [&](unsigned bits, bool valid) {
+            bits &= 0x7fffffffu;
+            if (!valid || bits == 0u) return;
+            int b = 0;
+            for (int q = 0; q < m; ++q) b += bits >= thr[q];
+            run.add(lsum, b, ln_f32_bits(bits));
+        });
+        run.flush(lsum);
+        __syncthreads();
+        if (tid == 0)
+            for (int q = 1; q <= m; ++q) lsum[q] += lsum[q - 1];
+        __syncthreads();
+        if (tid < n_steps) {
+            const int s = tid;
+            auto G = [&](int bidx, double u) -> double {
+                if (bidx == 0) return 0.0;
+                if (bidx == n_steps) return lsum[m];
+                const Target& t = tg[bidx - 1];
+                if (t.total) return lsum[m];
+                int j = 0;
+                while (j < m - 1 && thr[j] != t.prefix) ++j;
+                const double frac = u - (double)t.cnt_lt;
+                return lsum[j] + (frac != 0.0 ? frac * ln_f32_bits(t.prefix) : 0.0);
+            };
+            const double a = __dmul_rn(cw[s], (double)n);
+            const double b = __dmul_rn(cw[s + 1], (double)n);
+            double r = 0.0;
+            if (!(a < (double)s_zero)) r = exp((G(s + 1, b) - G(s, a)) / (w[s] * (double)n));
+            out[((size_t)row * K + k) * n_steps + s] = r;
+        }
+        return;
     }
 
     // ---- step means
@@ -435,8 +552,8 @@ int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, 
               double* cw) {
     if (n_rows < 1 || N < 1 || K < 1) return fail(MPSA_EINVAL, "build_odf: n_rows %d N %lld K %d", n_rows, (long long)N, K);
     if (n_steps < 1 || n_steps > kMaxSteps) return fail(MPSA_EINVAL, "build_odf: n_steps = %d (1..%d)", n_steps, kMaxSteps);
-    if (mean_kind != MPSA_MEAN_ARITH)
-        return fail(MPSA_EINVAL, "build_odf: mean_kind %d not available (arithmetic only)", mean_kind);
+    if (mean_kind != MPSA_MEAN_ARITH && mean_kind != MPSA_MEAN_GEOM)
+        return fail(MPSA_EINVAL, "build_odf: mean_kind %d (0 arithmetic, 1 geometric)", mean_kind);
     if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "build_odf: bounds outside [0, N]");
     for (int k = 0; k < K; ++k) {
         const int64_t len = bounds[k + 1] - bounds[k];
@@ -469,11 +586,11 @@ int odf_setup() {
 }
 
 int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* d_bounds, int n_steps,
-               const double* d_cw, const double* d_w, double* d_out, cudaStream_t st) {
+               const double* d_cw, const double* d_w, double* d_out, int mean_kind, cudaStream_t st) {
     int r;
     if ((r = odf_setup())) return r;
     k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w,
-                                                                         d_out);
+                                                                         d_out, mean_kind == MPSA_MEAN_GEOM);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }
@@ -497,7 +614,7 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_cw, cw.data(), (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_w, widths, n_steps * sizeof(double), cudaMemcpyHostToDevice, st));
     prof_mark(ctx, MPSA_KERNEL_ODF, st);
-    r = odf_launch(kappa, n_rows, N, K, d_b, n_steps, d_cw, d_w, odf_out, st);
+    r = odf_launch(kappa, n_rows, N, K, d_b, n_steps, d_cw, d_w, odf_out, mean_kind, st);
     prof_mark(ctx, MPSA_KERNEL_ODF, st);
     return r;
 }
@@ -552,8 +669,8 @@ extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_r
         return fail(MPSA_EINVAL, "build_odf_noalloc: n_rows %d N %lld K %d", n_rows, (long long)N, K);
     if (n_steps < 1 || n_steps > kMaxSteps)
         return fail(MPSA_EINVAL, "build_odf_noalloc: n_steps = %d (1..%d)", n_steps, kMaxSteps);
-    if (mean_kind != MPSA_MEAN_ARITH)
-        return fail(MPSA_EINVAL, "build_odf_noalloc: mean_kind %d not available (arithmetic only)", mean_kind);
+    if (mean_kind != MPSA_MEAN_ARITH && mean_kind != MPSA_MEAN_GEOM)
+        return fail(MPSA_EINVAL, "build_odf_noalloc: mean_kind %d (0 arithmetic, 1 geometric)", mean_kind);
     if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds outside [0, N]");
     for (int k = 0; k < K; ++k) {
         const int64_t len = bounds[k + 1] - bounds[k];
@@ -587,7 +704,7 @@ extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_r
     MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)odf_smem_bytes(kMaxSteps)));
     k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_b, n_steps, d_cw, d_w,
-                                                                         odf_out);
+                                                                         odf_out, mean_kind == MPSA_MEAN_GEOM);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }

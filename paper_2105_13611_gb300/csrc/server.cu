@@ -47,6 +47,7 @@ struct Req {
     std::vector<double> widths, cw;
     double* odf_out = nullptr;
     float* kc_out = nullptr;
+    int mean_kind = MPSA_MEAN_ARITH;
     // sizes
     int N = 0;
     size_t out_bytes = 0, kc_bytes = 0, est = 0;
@@ -154,7 +155,7 @@ int launch_odf(mpsa_server* s, Req* r, Slot& sl) {
         if ((rc = synth_rows(c, c->d_pop, nrow, dsel + off, r->grid.lambda0_nm, r->grid.R, N, kap, kc + off, nullptr,
                              nullptr, st)))
             return rc;
-        if ((rc = odf_launch(kap, nrow, N, K, db, ns, dcw, dw, dout + (size_t)off * K * ns, st))) return rc;
+        if ((rc = odf_launch(kap, nrow, N, K, db, ns, dcw, dw, dout + (size_t)off * K * ns, r->mean_kind, st))) return rc;
     }
     MPSA_CUDA_TRY(cudaMemcpyAsync(sl.pinned, dout, r->out_bytes, cudaMemcpyDeviceToHost, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync((char*)sl.pinned + r->out_bytes, kc, r->kc_bytes, cudaMemcpyDeviceToHost, st));
@@ -326,12 +327,13 @@ int mpsa_server_submit(mpsa_server* s, const mpsa_request* q, int64_t* ticket) {
             }
         if ((rc = check_grid(&q->grid, &r->N))) { delete r; return rc; }
         r->cw.resize(q->n_steps + 1);
-        if ((rc = odf_check(q->n_sel, r->N, q->K, q->bounds, q->n_steps, q->widths, MPSA_MEAN_ARITH, r->cw.data()))) {
+        if ((rc = odf_check(q->n_sel, r->N, q->K, q->bounds, q->n_steps, q->widths, q->mean_kind, r->cw.data()))) {
             delete r;
             return rc;
         }
         r->sel.assign(q->sel, q->sel + q->n_sel);
         r->grid = q->grid;
+        r->mean_kind = q->mean_kind;
         r->bounds.assign(q->bounds, q->bounds + q->K + 1);
         r->widths.assign(q->widths, q->widths + q->n_steps);
         r->odf_out = q->odf_out;

@@ -67,7 +67,7 @@ struct SpConst {
 
 __global__ void k_consts(int n_sel, const int* __restrict__ sel, int n_sp, const int* __restrict__ sp_el,
                          const int* __restrict__ sp_stage, int n_el, const double* __restrict__ el,
-                         const double* __restrict__ pop, double vturb, RowConst* __restrict__ rc,
+                         const double* __restrict__ pop, double vturb, int pop32, RowConst* __restrict__ rc,
                          SpConst* __restrict__ sc) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_sel * n_sp) return;
@@ -80,7 +80,10 @@ __global__ void k_consts(int n_sel, const int* __restrict__ sel, int n_sp, const
     const double NU = row[kPopHdr + 2 * e + st];
     const double pre = sqrt(kPI) * kE * kE / (kME * kC);
     SpConst o;
-    o.lnC = NU > 0 ? (float)(log(pre) + log(NU) - log(row[kPopRho])) : -INFINITY;
+    if (pop32)   // precision-study variant: the population table rounded to FP32 first
+        o.lnC = NU > 0 ? (float)log(pre) + logf((float)NU) - logf((float)row[kPopRho]) : -INFINITY;
+    else
+        o.lnC = NU > 0 ? (float)(log(pre) + log(NU) - log(row[kPopRho])) : -INFINITY;
     o.u = (float)u;
     o.kv = (float)(kC / u);
     sc[t] = o;
@@ -183,35 +186,56 @@ __device__ float v_bound(float a, float t) {
     return fmaxf(sqrtf(8.f * a * kInvSqrtPi / t), 2.f * sqrtf(logf(fmaxf(2.f / t, 1.f)))) * 1.01f + 1.f;
 }
 
+// Crossing of H(v, a) = t by the Illinois variant of regula falsi on ln H against ln v.
+// Invariant: H(e^xlo) >= t > H(e^xhi); the bracket shrinks to a few FP32 ulps of ln v
+// (typically 6-10 evaluations instead of 40 bisection steps).  Returns the verified ends.
+__device__ void crossing(float a, float t, float vb, float* v_ge, float* v_lt) {
+    const float lt = logf(t);
+    auto f = [&](float x) {
+        const float h = voigt_H(expf(x), a);
+        return h > 0.f ? logf(h) - lt : -1.0e4f;
+    };
+    float xlo = logf(1e-4f), xhi = logf(vb);
+    float flo = f(xlo), fhi = f(xhi);
+    if (flo < 0.f) {                       // below t already at |v| = 1e-4
+        *v_ge = -1.f;
+        *v_lt = 1e-4f;
+        return;
+    }
+    int side = 0;
+    // stop at ~2 FP32 ulps of ln v (the ends stay verified, so precision only sets tightness)
+    for (int it = 0; it < 60 && xhi - xlo > 3e-7f * fmaxf(1.f, fabsf(xhi)); ++it) {
+        float x = (xlo * fhi - xhi * flo) / (fhi - flo);
+        if (!(x > xlo && x < xhi)) x = 0.5f * (xlo + xhi);
+        if (!(x > xlo && x < xhi)) break;
+        const float fx = f(x);
+        if (fx >= 0.f) {
+            xlo = x;
+            flo = fx;
+            if (side == 1) fhi *= 0.5f;
+            side = 1;
+        } else {
+            xhi = x;
+            fhi = fx;
+            if (side == -1) flo *= 0.5f;
+            side = -1;
+        }
+    }
+    *v_ge = expf(xlo);
+    *v_lt = expf(xhi);
+}
+
 __device__ void cut_speeds(float a, float r, float* v_out, float* v_in) {
     const float t_out = r * (1.f - 1e-4f), t_in = r * (1.f + 1e-4f);
-    const float vmin = 1e-4f;
-    {
-        float lo = vmin, hi = v_bound(a, t_out);
-        if (voigt_H(lo, a) < t_out) {
-            hi = lo;
-        } else {
-            for (int it = 0; it < 40; ++it) {
-                const float mid = sqrtf(lo * hi);
-                if (voigt_H(mid, a) < t_out) hi = mid; else lo = mid;
-            }
-        }
-        *v_out = hi;
-    }
+    float ge, lt;
+    crossing(a, t_out, v_bound(a, t_out), &ge, &lt);
+    *v_out = lt;
     if (voigt_H(0.f, a) < t_in) {
         *v_in = -1.f;
-    } else {
-        float lo = vmin, hi = v_bound(a, t_in);
-        if (voigt_H(lo, a) < t_in) {
-            *v_in = 0.f;
-            return;
-        }
-        for (int it = 0; it < 40; ++it) {
-            const float mid = sqrtf(lo * hi);
-            if (voigt_H(mid, a) < t_in) hi = mid; else lo = mid;
-        }
-        *v_in = lo;
+        return;
     }
+    crossing(a, t_in, v_bound(a, t_in), &ge, &lt);
+    *v_in = ge < 0.f ? 0.f : ge;
 }
 
 // grid offsets d >= 0 at which |v| reaches vv, red side (d > 0: |v| = kv (1 - e^{-d lnq}))
@@ -432,6 +456,7 @@ constexpr int kFlMask = (1 << kFlKloBits) - 1;
 constexpr int kFlChk = 1 << 10;      // points near the cut: test s_rel H >= 1
 constexpr int kFlAlt = 1 << 11;      // far: "y" form; near: expm1 series for v
 constexpr int kFlFull = 1 << 12;     // the window covers every slot of the tile
+constexpr int kFlRat = 1 << 13;      // far: rational form sk / (|z|^2 - 3/2)
 
 struct NearRec {
     float cf, f, klnq, a, srel, kv;
@@ -440,16 +465,22 @@ struct NearRec {
     int pad[3];
 };
 
-// far line.  With v' = sqrt(2) v = G_k * (sqrt2 kv B) + sqrt2 kv E1 (exact expm1 split
-// around the tile start) and D = v'^2 + 2a^2 - 1 = 2|z|^2 - 1, the far tier is
-//   s_rel H = (2 sk D + 4 sk) / (D^2 + 8 a^2)        ("exact" form, sk = s_rel a/sqrt(pi)),
-// which is the one-level continued fraction without truncation: 5 FFMA + 1 reciprocal.
-// Where D^2 could overflow FP32 (|v| >= 1e9 somewhere in the tile) the "y" form
-// y = 1/D, s_rel H = sk y (2 + 4 y) is used; there 8 a^2 y^2 is far below 1e-8.
+// far line, three forms (sk = s_rel a / sqrt(pi)).  v = G_k * (kv B) + kv E1 is the exact
+// expm1 split of the frequency offset around the tile start.
+//  * kFarRat, "rational": s_rel H = sk / (|z|^2 - 3/2), |z|^2 = v^2 + a^2.  Its relative
+//    error against H is below (2 + 2a^2)/|z|^4 (the asymptotic series of H to order |z|^-4),
+//    so it is used where that bound is <= 1e-6 over the whole tile: 3 FFMA + 1 reciprocal.
+//    p = {kv B, kv E1, a^2 - 3/2, sk}.
+//  * kFarExact: the one-level continued fraction without truncation, with
+//    v' = sqrt2 v and D = v'^2 + 2a^2 - 1 = 2|z|^2 - 1:
+//    s_rel H = (2 sk D + 4 sk) / (D^2 + 8 a^2): 5 FFMA + 1 reciprocal.
+//  * kFarY: where D^2 could overflow FP32 (|v| >= 1e9 somewhere in the tile),
+//    y = 1/D, s_rel H = sk y (2 + 4 y); there 8 a^2 y^2 is far below 1e-8.
+//    p = {sqrt2 kv B, sqrt2 kv E1, 2a^2 - 1, 8a^2}, q = {2 sk, 4 sk} for both.
 // The PTS points are evaluated without branches so that their dependency chains
 // interleave; MASKED lines (partial coverage or points near the cut) select with a mask.
-// p = {sqrt2 kv B, sqrt2 kv E1, 2a^2 - 1, 8a^2}, q = {2 sk, 4 sk}.
-template <int PTS, bool YFORM, bool MASKED>
+constexpr int kFarRat = 0, kFarExact = 1, kFarY = 2;
+template <int PTS, int FORM, bool MASKED>
 __device__ __forceinline__ void far_line(const float4 p, const float2 q, int klo, int khi, bool chk,
                                          const float (&G)[PTS], float (&part)[PTS]) {
 #pragma unroll
@@ -457,7 +488,10 @@ __device__ __forceinline__ void far_line(const float4 p, const float2 q, int klo
         const float vp = fmaf(G[k], p.x, p.y);
         const float D = fmaf(vp, vp, p.z);
         float t, y;
-        if (YFORM) {
+        if (FORM == kFarRat) {
+            y = rcp_approx(D);
+            t = p.w;
+        } else if (FORM == kFarY) {
             y = rcp_approx(D);
             t = fmaf(q.y, y, q.x);
         } else {
@@ -505,7 +539,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
     __shared__ float4 sFarA[THREADS];
     __shared__ float4 sFarB[THREADS];
     __shared__ NearRec sNear[THREADS];
-    __shared__ int sCnt[2][THREADS / 32];
+    __shared__ int sCnt[5][THREADS / 32];
 
     const int J0 = tile * TILE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -569,8 +603,15 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                         const float vmax = fmaxf(fabsf(kv * E1), fabsf(kv * expm1f(-xe)));
                         const bool yform = vmax >= 1.0e9f;
                         const float sk = srel * a * kInvSqrtPi;
-                        fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
-                        fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
+                        // rational form where (2 + 2a^2) / |z|^4 <= 1e-6 at the tile's nearest point
+                        const float zmin2 = fmaf(vmin, vmin, A);
+                        if (zmin2 * zmin2 >= 1.0e6f * fmaf(2.f, A, 2.f)) {
+                            fa = make_float4(kv * B, kv * E1, A - 1.5f, sk);
+                            fb = make_float4(0.f, 0.f, __int_as_float(flags | kFlRat), 0.f);
+                        } else {
+                            fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
+                            fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
+                        }
                     } else {
                         isNear = true;
                         const float dmax = fmaxf(fabsf((float)(P0 - c) - f), fabsf((float)(P1 - c) - f));
@@ -588,44 +629,72 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                     }
                 }
             }
-            const unsigned bf = __ballot_sync(0xffffffffu, isFar), bn = __ballot_sync(0xffffffffu, isNear);
-            if (lane == 0) {
-                sCnt[0][warp] = __popc(bf);
-                sCnt[1][warp] = __popc(bn);
+            // far lines are compacted into four lists: plain rational, plain "exact" and plain
+            // "y" forms, and masked (partial coverage or cut test), so the hot loops dispatch
+            // nothing; near lines into a fifth
+            int cat = -1;
+            if (isFar) {
+                const int fl = __float_as_int(fb.z);
+                const bool plain = (fl & kFlFull) && !(fl & kFlChk);
+                cat = plain ? ((fl & kFlRat) ? 0 : ((fl & kFlAlt) ? 2 : 1)) : 3;
+            } else if (isNear) {
+                cat = 4;
+            }
+            unsigned bm = 0u;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const unsigned b = __ballot_sync(0xffffffffu, cat == q);
+                if (cat == q) bm = b;
+                if (lane == 0) sCnt[q][warp] = __popc(b);
             }
             __syncthreads();
-            int offF = 0, offN = 0, nFar = 0, nNear = 0;
+            int off = 0, tot[5] = {0, 0, 0, 0, 0};
 #pragma unroll
             for (int w = 0; w < THREADS / 32; ++w) {
-                const int cf = sCnt[0][w], cn = sCnt[1][w];
-                if (w < warp) { offF += cf; offN += cn; }
-                nFar += cf;
-                nNear += cn;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const int cnt = sCnt[q][w];
+                    if (w < warp && q == cat) off += cnt;
+                    tot[q] += cnt;
+                }
             }
             const unsigned lt = (1u << lane) - 1u;
-            if (isFar) {
-                const int p = offF + __popc(bf & lt);
+            if (cat >= 0 && cat < 4) {
+                int base2 = 0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (q < cat) base2 += tot[q];
+                const int p = base2 + off + __popc(bm & lt);
                 sFarA[p] = fa;
                 sFarB[p] = fb;
             }
-            if (isNear) sNear[offN + __popc(bn & lt)] = nr;
+            if (cat == 4) sNear[off + __popc(bm & lt)] = nr;
+            const int nNear = tot[4];
             __syncthreads();
 
             // ---- evaluation: every thread, every compacted line, its PTS points
-            for (int r = 0; r < nFar; ++r) {
-                const float4 p = sFarA[r];
-                const float4 q4 = sFarB[r];
-                const float2 q = make_float2(q4.x, q4.y);
-                const int fl = __float_as_int(q4.z);
-                const int klo = fl & kFlMask, khi = (fl >> kFlKloBits) & kFlMask;
-                const bool chk = fl & kFlChk, yform = fl & kFlAlt;
-                const bool plain = (fl & kFlFull) && !chk;     // all points, no cut test
-                if (yform) {
-                    if (plain) far_line<PTS, true, false>(p, q, klo, khi, chk, G, part);
-                    else far_line<PTS, true, true>(p, q, klo, khi, chk, G, part);
-                } else {
-                    if (plain) far_line<PTS, false, false>(p, q, klo, khi, chk, G, part);
-                    else far_line<PTS, false, true>(p, q, klo, khi, chk, G, part);
+            {
+                int r = 0;
+                for (; r < tot[0]; ++r)
+                    far_line<PTS, kFarRat, false>(sFarA[r], make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                for (; r < tot[0] + tot[1]; ++r) {
+                    const float4 q4 = sFarB[r];
+                    far_line<PTS, kFarExact, false>(sFarA[r], make_float2(q4.x, q4.y), 0, PTS - 1, false, G, part);
+                }
+                for (; r < tot[0] + tot[1] + tot[2]; ++r) {
+                    const float4 q4 = sFarB[r];
+                    far_line<PTS, kFarY, false>(sFarA[r], make_float2(q4.x, q4.y), 0, PTS - 1, false, G, part);
+                }
+                for (; r < tot[0] + tot[1] + tot[2] + tot[3]; ++r) {
+                    const float4 p = sFarA[r];
+                    const float4 q4 = sFarB[r];
+                    const float2 q = make_float2(q4.x, q4.y);
+                    const int fl = __float_as_int(q4.z);
+                    const int klo = fl & kFlMask, khi = (fl >> kFlKloBits) & kFlMask;
+                    const bool chk = fl & kFlChk;
+                    if (fl & kFlRat) far_line<PTS, kFarRat, true>(p, q, klo, khi, chk, G, part);
+                    else if (fl & kFlAlt) far_line<PTS, kFarY, true>(p, q, klo, khi, chk, G, part);
+                    else far_line<PTS, kFarExact, true>(p, q, klo, khi, chk, G, part);
                 }
             }
             const int seg0 = J0 + warp * 32;
@@ -738,7 +807,113 @@ __global__ void __launch_bounds__(THREADS, MINB) k_tiles_persistent(const RowDes
     }
 }
 
+// ---------------------------------------------------------------------------
+// All-FP64 variant of the profile kernel (precision study): line terms of Eq. (l_nu_line),
+// the exact frequency offset v = (c/lambda_j - nu0)/dnuD and H in FP64, plain FP64 sums.
+// Same candidate lines and outer windows as the FP32 kernel; the cut threshold is the FP32
+// one (t_p = exp(ln t_p)), so inclusion decisions differ only inside the edge slack band.
+struct Tile64Args {
+    TileArgs t;
+    const int* sel;
+    const double* pop;
+    int pop_stride_;
+    int n_sp;
+    const int* sp_el;
+    const int* sp_stage;
+    const double* el;          // [5][n_el]
+    int n_el;
+    double vturb;
+    const double* lam_nm;      // line list
+    const float* loggf;
+    const float* E;
+    const float* lgR;
+    const float* lgS;
+    const float* lgW;
+    const int* species;
+    double lam0_nm, lnq64;
+};
+
+__global__ void __launch_bounds__(256) k_tiles64(Tile64Args g) {
+    constexpr int THREADS = 256, PTS = kPtsPerThread, TILE = THREADS * PTS;
+    __shared__ double sS[THREADS], sA[THREADS], sNu[THREADS], sDnu[THREADS];
+    __shared__ int sLo[THREADS], sHi[THREADS];
+    __shared__ int sN;
+    const int s = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+    const RowDesc r = row_desc(g.t, s, kTile);
+    const int J0 = tile * TILE;
+    const double* row = g.pop + (size_t)g.sel[s] * g.pop_stride_;
+    const double T = row[kPopT], ne = row[kPopNe], nHI = row[kPopNHI], rho = row[kPopRho];
+    const double tp = exp((double)*r.ln_tp);
+    double nu[PTS], acc[PTS];
+    for (int k = 0; k < PTS; ++k) {
+        const int j = J0 + k * THREADS + tid;
+        nu[k] = kC / (g.lam0_nm * exp((double)j * g.lnq64) * 1e-7);
+        acc[k] = 0.0;
+    }
+    const double pre = sqrt(kPI) * kE * kE / (kME * kC);
+    for (int b = 0; b < kNumClasses; ++b) {
+        const int reach = 1 << b;
+        int tlo = max(floordiv(J0 - reach + 1, TILE), -1), thi = min(floordiv(J0 + TILE - 1 + reach - 1, TILE), r.nT);
+        if (tlo > thi) continue;
+        const int* cum = r.cum + (size_t)b * (r.nT + 3);
+        const int beg = cum[tlo + 1], end = cum[thi + 2];
+        for (int base = beg; base < end; base += THREADS) {
+            if (tid == 0) sN = 0;
+            __syncthreads();
+            const int pos = base + tid;
+            if (pos < end) {
+                const int q = r.bidx[pos];
+                const int jlo = r.jlo[q], jhi = r.jhi[q];
+                if (jhi >= J0 && jlo <= J0 + TILE - 1) {
+                    const int sp = g.species[q];
+                    const int e = g.sp_el[sp], st = g.sp_stage[sp];
+                    const double lam = g.lam_nm[q] * 1e-7;
+                    const double nu0 = kC / lam;
+                    const double u = sqrt(2.0 * kKB * T / (g.el[e] * kAMU) + g.vturb * g.vturb);
+                    const double dnu = nu0 * u / kC;
+                    const double gam = pow(10.0, (double)g.lgR[q]) + pow(10.0, (double)g.lgS[q]) * ne +
+                                       pow(10.0, (double)g.lgW[q]) * nHI;
+                    const double NU = row[kPopHdr + 2 * e + st];
+                    const double S = pre * pow(10.0, (double)g.loggf[q]) * NU / (rho * dnu) *
+                                     exp(-(double)g.E[q] * kEV / (kKB * T)) * (-expm1(-kH * nu0 / (kKB * T)));
+                    const int slot = atomicAdd(&sN, 1);
+                    sS[slot] = S;
+                    sA[slot] = gam / (4.0 * kPI * dnu);
+                    sNu[slot] = nu0;
+                    sDnu[slot] = dnu;
+                    sLo[slot] = jlo;
+                    sHi[slot] = jhi;
+                }
+            }
+            __syncthreads();
+            const int n = sN;
+            for (int i = 0; i < n; ++i) {
+                const double S = sS[i], a = sA[i], nu0 = sNu[i], dnu = sDnu[i];
+                const int lo = sLo[i], hi = sHi[i];
+                for (int k = 0; k < PTS; ++k) {
+                    const int j = J0 + k * THREADS + tid;
+                    if (j < lo || j > hi) continue;
+                    const double l = S * voigt_H64((nu[k] - nu0) / dnu, a);
+                    if (l >= tp) acc[k] += l;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = 0; k < PTS; ++k) {
+        const int j = J0 + k * THREADS + tid;
+        if (j < r.N) r.out[j] = (float)acc[k];
+    }
+}
+
 int g_init_mask = 0;
+
+__global__ void k_voigt_eval(int64_t n, const double* __restrict__ v, const double* __restrict__ a, bool fp64,
+                             double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = fp64 ? voigt_H64(v[i], a[i]) : (double)voigt_H((float)v[i], (float)a[i]);
+}
 
 }  // namespace
 
@@ -806,8 +981,9 @@ int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const
     const int n_sel = b.n_sel, n_sp = ctx->n_sp;
     const int lb = (int)((L + 255) / 256);
     k_place<<<lb, 256, 0, st>>>(L, ctx->d_lam, lam0_nm, b.lnq, b.c, b.f, b.lamcm);
+    const int pop32 = (opts && opts->precision == MPSA_PREC_FP32_POP32) ? 1 : 0;
     k_consts<<<(n_sel * n_sp + 127) / 128, 128, 0, st>>>(n_sel, d_sel, n_sp, ctx->d_sp_el, ctx->d_sp_stage, ctx->n_el,
-                                                           ctx->d_el, pop, ctx->vturb, b.rc, b.spc);
+                                                           ctx->d_el, pop, ctx->vturb, pop32, b.rc, b.spc);
     k_kappa0<<<dim3(lb, n_sel), 256, 0, st>>>(L, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS,
                                                ctx->d_lgW, b.lamcm, n_sp, b.rc, b.spc, b.lnS, b.av, b.lnk0);
     k_median<<<n_sel, 1024, 0, st>>>(L, b.lnk0, (float)log(kcf), (float)log(cut), b.ln_tp, kc_out);
@@ -855,7 +1031,8 @@ TileArgs tile_args(const PrepBufs& b, float* kappa) {
 int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
                float* kappa, float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st) {
     const int prec = opts ? opts->precision : 0;
-    if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE)
+    if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE && prec != MPSA_PREC_FP64 &&
+        prec != MPSA_PREC_FP32_POP32)
         return fail(MPSA_EINVAL, "synth: precision %d", prec);
     Scratch sc(st);
     PrepBufs b;
@@ -864,7 +1041,29 @@ int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, do
     if ((r = prep_launch(b, ctx, pop, d_sel, lam0_nm, kc_out, evals, opts, st))) return r;
     const TileArgs ta = tile_args(b, kappa);
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);
-    if (prec == MPSA_PREC_FP32_NAIVE) k_tiles<MPSA_PREC_FP32_NAIVE><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
+    if (prec == MPSA_PREC_FP64) {
+        Tile64Args g;
+        g.t = ta;
+        g.sel = d_sel;
+        g.pop = pop;
+        g.pop_stride_ = pop_stride(ctx->n_el);
+        g.n_sp = ctx->n_sp;
+        g.sp_el = ctx->d_sp_el;
+        g.sp_stage = ctx->d_sp_stage;
+        g.el = ctx->d_el;
+        g.n_el = ctx->n_el;
+        g.vturb = ctx->vturb;
+        g.lam_nm = ctx->d_lam;
+        g.loggf = ctx->d_loggf;
+        g.E = ctx->d_E;
+        g.lgR = ctx->d_lgR;
+        g.lgS = ctx->d_lgS;
+        g.lgW = ctx->d_lgW;
+        g.species = ctx->d_species;
+        g.lam0_nm = lam0_nm;
+        g.lnq64 = b.lnq;
+        k_tiles64<<<dim3(b.nT, n_sel), 256, 0, st>>>(g);
+    } else if (prec == MPSA_PREC_FP32_NAIVE) k_tiles<MPSA_PREC_FP32_NAIVE><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
     else k_tiles<MPSA_PREC_FP32_COMPENSATED><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);
     MPSA_CUDA_TRY(cudaGetLastError());
@@ -998,7 +1197,7 @@ struct mpsa_batch {
         int64_t* evals = nullptr;
         mpsa::PrepBufs pb;
         int* cum = nullptr;   // tile ranges for the chosen tile size
-        int K = 0, n_steps = 0;
+        int K = 0, n_steps = 0, mean_kind = MPSA_MEAN_ARITH;
         int64_t* d_bounds = nullptr;
         double *d_cw = nullptr, *d_w = nullptr, *odf = nullptr;
     };
@@ -1094,9 +1293,10 @@ int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int au
         if (q.K > 0) {
             if (!q.bounds || !q.widths || !q.odf_out) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d ODF args", g);
             std::vector<double> cw(q.n_steps >= 1 && q.n_steps <= 32 ? q.n_steps + 1 : 1);
-            if ((r = odf_check(q.n_sel, G.N, q.K, q.bounds, q.n_steps, q.widths, MPSA_MEAN_ARITH, cw.data()))) return r;
+            if ((r = odf_check(q.n_sel, G.N, q.K, q.bounds, q.n_steps, q.widths, q.mean_kind, cw.data()))) return r;
             G.K = q.K;
             G.n_steps = q.n_steps;
+            G.mean_kind = q.mean_kind;
             G.odf = q.odf_out;
             if ((r = balloc(b, &G.d_bounds, q.K + 1)) || (r = balloc(b, &G.d_cw, q.n_steps + 1)) ||
                 (r = balloc(b, &G.d_w, q.n_steps)))
@@ -1213,7 +1413,7 @@ int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int au
     if (rc == MPSA_OK) rc = persistent_launch(b->cfg, b->prec, b->d_rows, b->d_units, b->n_units, b->d_counter, cap);
     if (rc == MPSA_OK)
         for (auto& G : b->groups)
-            if (G.K > 0 && (rc = odf_launch(G.kappa, G.n_sel, G.N, G.K, G.d_bounds, G.n_steps, G.d_cw, G.d_w, G.odf, cap)))
+            if (G.K > 0 && (rc = odf_launch(G.kappa, G.n_sel, G.N, G.K, G.d_bounds, G.n_steps, G.d_cw, G.d_w, G.odf, G.mean_kind, cap)))
                 break;
     e = cudaStreamEndCapture(cap, &b->graph);
     cudaStreamDestroy(cap);
@@ -1270,6 +1470,19 @@ int mpsa_batch_get_info(const mpsa_batch* b, mpsa_batch_info* out) {
     out->n_units = b->n_units;
     out->n_tuned = b->n_tuned;
     for (int k = 0; k < 8; ++k) out->tune_ms_per_mpoint[k] = k < kNumCfgs ? b->tune_ms_per_mpt[k] : 0.0;
+    return MPSA_OK;
+}
+
+int mpsa_voigt(mpsa_ctx* ctx, const double* v, const double* a, int64_t n, int32_t precision, double* out,
+               void* stream) {
+    if (!ctx || n < 0 || (n > 0 && (!v || !a || !out))) return fail(MPSA_EINVAL, "mpsa_voigt: bad argument");
+    if (n == 0) return MPSA_OK;
+    MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
+    const int threads = 256;
+    const int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 0x7fffffff) return fail(MPSA_EINVAL, "mpsa_voigt: n = %lld too large", (long long)n);
+    k_voigt_eval<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(n, v, a, precision == MPSA_PREC_FP64, out);
+    MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }
 

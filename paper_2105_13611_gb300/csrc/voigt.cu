@@ -27,6 +27,57 @@ void hermite(int n, double x, double* hn, double* hn1) {
 
 }  // namespace
 
+namespace {
+// positive roots and weights of the n-point Gauss-Hermite rule (n even)
+int gauss_hermite(int n, double* nodes, double* weights) {
+    const int half = n / 2;
+    int found = 0;
+    const double xmax = sqrt(2.0 * n + 1.0) + 1.0;
+    const int steps = 40000;
+    double xprev = 1e-9, hprev, dummy;
+    hermite(n, xprev, &hprev, &dummy);
+    for (int i = 1; i <= steps && found < half; ++i) {
+        double x = xmax * i / steps, h;
+        hermite(n, x, &h, &dummy);
+        if ((h > 0) != (hprev > 0)) {
+            double lo = xprev, hi = x, hlo = hprev;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi), hm;
+                hermite(n, mid, &hm, &dummy);
+                if ((hm > 0) == (hlo > 0)) { lo = mid; hlo = hm; } else { hi = mid; }
+            }
+            nodes[found++] = 0.5 * (lo + hi);
+        }
+        xprev = x;
+        hprev = h;
+    }
+    if (found != half) return fail(MPSA_EINVAL, "gauss_hermite(%d): found %d roots", n, found);
+    // omega_k = 2^{n-1} n! sqrt(pi) / (n^2 H_{n-1}(x_k)^2), in logs to avoid overflow
+    double lfact = 0.0;
+    for (int k = 2; k <= n; ++k) lfact += log((double)k);
+    for (int k = 0; k < half; ++k) {
+        double hn, hn1;
+        hermite(n, nodes[k], &hn, &hn1);
+        weights[k] = exp((n - 1) * log(2.0) + lfact + 0.5 * log(kPI) - 2.0 * log((double)n) - 2.0 * log(fabs(hn1)));
+    }
+    return MPSA_OK;
+}
+}  // namespace
+
+int voigt_host_consts64(VoigtConsts64* out) {
+    double nodes[kGHPairs64], weights[kGHPairs64];
+    int r = gauss_hermite(2 * kGHPairs64, nodes, weights);
+    if (r != MPSA_OK) return r;
+    const double dl = kGHDelta64;
+    const double pre = exp(dl * dl) / kPI;
+    for (int k = 0; k < kGHPairs64; ++k) {
+        out->s[k] = nodes[k];
+        out->U[k] = pre * weights[k] * cos(2.0 * dl * nodes[k]);
+        out->S[k] = pre * weights[k] * sin(2.0 * dl * nodes[k]);
+    }
+    return MPSA_OK;
+}
+
 int voigt_host_consts(VoigtConsts* out) {
     const int n = 2 * kGHPairs;
     double nodes[kGHPairs], weights[kGHPairs];

@@ -44,15 +44,30 @@ struct VoigtConsts {
 // Host: the constants from the Hermite nodes and weights (voigt.cu).
 int voigt_host_consts(VoigtConsts* out);
 
+// FP64 Voigt for the all-FP64 precision variant: the Laplace continued fraction with 4
+// levels for |z|^2 >= 1600 and 16 levels for 36 <= |z|^2 < 1600 (relative error 1.1e-12),
+// and the 32-point shifted Gauss-Hermite sum with delta = 2 below (region II for a < 1,
+// region I above; 5e-14).
+constexpr int kGHPairs64 = 16;
+constexpr double kGHDelta64 = 2.0;
+struct VoigtConsts64 {
+    double s[kGHPairs64], U[kGHPairs64], S[kGHPairs64];
+};
+int voigt_host_consts64(VoigtConsts64* out);
+
 // Every translation unit that evaluates H keeps its own copy of the constants;
 // it uploads them with voigt_upload() once per device before its first launch.
 static __constant__ VoigtConsts c_voigt;
+static __constant__ VoigtConsts64 c_voigt64;
 
 static inline int voigt_upload() {
     VoigtConsts h;
+    VoigtConsts64 h64;
     int rc = voigt_host_consts(&h);
+    if (rc == MPSA_OK) rc = voigt_host_consts64(&h64);
     if (rc != MPSA_OK) return rc;
     cudaError_t e = cudaMemcpyToSymbol(c_voigt, &h, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_voigt64, &h64, sizeof(h64));
     return e == cudaSuccess ? MPSA_OK : fail(MPSA_ECUDA, "cudaMemcpyToSymbol(c_voigt): %s", cudaGetErrorString(e));
 }
 
@@ -62,8 +77,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// far tier.  V = v^2, A = a^2, ka = a/sqrt(pi).
+// far tier (|z|^2 >= 1600).  V = v^2, A = a^2, ka = a/sqrt(pi).  Where (2 + 2A)/|z|^4 <= 1e-6
+// the rational form ka / (|z|^2 - 3/2) (relative error below that bound, from the asymptotic
+// series of H to order |z|^-4); otherwise the one-level continued fraction in y = 1/(2|z|^2 - 1)
+// with its 8A y^2 correction.
 __device__ __forceinline__ float voigt_far(float V, float A, float ka) {
+    const float Z = V + A;
+    if (Z * Z >= 1.0e6f * fmaf(2.f, A, 2.f)) return ka * rcp_approx(Z - 1.5f);
     float y = rcp_approx(fmaf(2.f, V, fmaf(2.f, A, -1.f)));
     float e = 8.f * A * y * y;
     return ka * y * fmaf(4.f, y, 2.f) * fmaf(e, e - 1.f, 1.f);
@@ -135,6 +155,44 @@ __device__ __forceinline__ float voigt_H_lean(float v, float a) {
     const float V = v * v, A = a * a;
     if (V + A >= 1600.f) return voigt_far(V, A, a * kInvSqrtPi);
     return voigt_inner_tiers(v, a);
+}
+
+// FP64 H(v, a) (see VoigtConsts64).
+__device__ inline double voigt_H64(double v, double a) {
+    v = fabs(v);
+    const double Z = v * v + a * a;
+    if (Z >= 36.0) {
+        double tr = v, ti = a;
+        const int levels = Z >= 1600.0 ? 4 : 16;   // 4 levels reach 1e-14 for |z| >= 40
+        for (int k = levels; k >= 1; --k) {
+            const double m = 0.5 * k / (tr * tr + ti * ti);
+            const double ntr = v - m * tr;
+            ti = a + m * ti;
+            tr = ntr;
+        }
+        double h = ti / (1.7724538509055160273 * (tr * tr + ti * ti));
+        if (a < 1e-2) h += exp(a * a - v * v) * cos(2.0 * v * a);
+        return h;
+    }
+    const double d = kGHDelta64;
+    const double Y1 = a + d, Y12 = Y1 * Y1;
+    double sum = 0.0;
+    if (a < 1.0) {
+        const double dY = Y1 * d, Yd = Y1 + d, d2 = d * d;
+        for (int k = 0; k < kGHPairs64; ++k) {
+            const double sk = c_voigt64.s[k], Uk = c_voigt64.U[k], Sk = c_voigt64.S[k];
+            const double r = v - sk, rp = v + sk, r2 = r * r, rp2 = rp * rp;
+            sum += (Uk * (r2 - dY) + Sk * r * Yd) / ((r2 + d2) * (r2 + Y12)) +
+                   (Uk * (rp2 - dY) - Sk * rp * Yd) / ((rp2 + d2) * (rp2 + Y12));
+        }
+        return exp(-v * v) + a * sum;
+    }
+    for (int k = 0; k < kGHPairs64; ++k) {
+        const double sk = c_voigt64.s[k], Uk = c_voigt64.U[k], Sk = c_voigt64.S[k];
+        const double r = v - sk, rp = v + sk;
+        sum += (Uk * Y1 - Sk * r) / (r * r + Y12) + (Uk * Y1 + Sk * rp) / (rp * rp + Y12);
+    }
+    return sum;
 }
 
 }  // namespace mpsa

@@ -20,20 +20,22 @@ def test_batch_matches_per_call_and_replays():
     nP = len(w.T)
     grids = [wl.Grid(300.0, 303.0, 2e6), wl.Grid(301.0, 301.7, 5e5)]
     sels = [[0, 5, 2, 7], [6, 1, 3]]
+    means = [binding.MEAN_ARITH, binding.MEAN_GEOM]
     groups, ref = [], []
-    for g, sel in zip(grids, sels):
+    for g, sel, mk in zip(grids, sels, means):
         N = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
         kap = torch.full((len(sel), N), -1.0, dtype=torch.float32, device="cuda")
         kc = torch.empty(len(sel), dtype=torch.float32, device="cuda")
         b = wl.equal_intervals(N, 3)
         odf = torch.empty((len(sel), 3, 12), dtype=torch.float64, device="cuda")
-        groups.append(dict(grid=g, sel=sel, kappa=kap, kappa_c=kc, bounds=b, widths=wl.ODF_WIDTHS_12, odf=odf))
+        groups.append(dict(grid=g, sel=sel, kappa=kap, kappa_c=kc, bounds=b, widths=wl.ODF_WIDTHS_12, odf=odf,
+                           mean_kind=mk))
         # per-call reference
         k2 = torch.empty_like(kap)
         kc2 = torch.empty_like(kc)
         ctx.synth_opacity(g, sel, k2, kc2)
         o2 = torch.empty_like(odf)
-        ctx.build_odf(k2, b, wl.ODF_WIDTHS_12, o2)
+        ctx.build_odf(k2, b, wl.ODF_WIDTHS_12, o2, mean_kind=mk)
         ref.append((k2, kc2, o2))
     batch = binding.Batch(ctx, groups, autotune=True)
     info = batch.info()

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 W12 = wl.ODF_WIDTHS_12
 
 
-def gpu_odf(kappa_np, bounds, widths):
+def gpu_odf(kappa_np, bounds, widths, mean="arith"):
     import torch
     from paper_2105_13611_gb300 import binding
     ctx = binding.Context(0)
@@ -20,17 +20,17 @@ def gpu_odf(kappa_np, bounds, widths):
     if k.ndim == 1:
         k = k[None, :]
     out = torch.empty((k.shape[0], len(bounds) - 1, len(widths)), dtype=torch.float64, device="cuda")
-    ctx.build_odf(k, bounds, widths, out)
+    ctx.build_odf(k, bounds, widths, out, mean_kind=binding.MEAN_GEOM if mean == "geom" else binding.MEAN_ARITH)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
 
-def check(kappa, bounds, widths, rtol=ODF_RTOL):
+def check(kappa, bounds, widths, rtol=ODF_RTOL, mean="arith"):
     kappa = np.asarray(kappa, dtype=np.float32)
-    g = gpu_odf(kappa, bounds, widths)
+    g = gpu_odf(kappa, bounds, widths, mean)
     rows = kappa[None, :] if kappa.ndim == 1 else kappa
     for r in range(rows.shape[0]):
-        o = od.odf(rows[r].astype(np.float64), bounds, widths)
+        o = od.odf(rows[r].astype(np.float64), bounds, widths, mean=mean)
         scale = np.maximum(np.abs(o), 1e-300)
         rel = np.abs(g[r] - o) / scale
         ok = (rel <= rtol) | ((o == 0) & (g[r] == 0))
@@ -45,18 +45,20 @@ def test_random_lognormal_intervals():
     assert np.all(np.diff(g, axis=2) >= 0)
 
 
-def test_adversarial():
-    n = 5000
+def adversarial_cases(n=5000):
     rng = np.random.default_rng(2)
-    cases = [np.zeros(n), np.full(n, 3.5), np.r_[np.zeros(n - 1), 1e30], np.repeat([1.0, 2.0, 3.0], [2000, 1, 2999]),
+    return [np.zeros(n), np.full(n, 3.5), np.r_[np.zeros(n - 1), 1e30], np.repeat([1.0, 2.0, 3.0], [2000, 1, 2999]),
              np.r_[np.zeros(n // 2), np.ones(n - n // 2)], rng.integers(0, 3, n).astype(float),
              np.r_[1e-40 * np.ones(100), rng.lognormal(0, 1, n - 100)],          # denormals
              rng.lognormal(-80, 10, n),                                          # very small and wide
              1.0 + 1e-2 * rng.random(n),                                         # narrow: 1 % spread
              1.0 + 1e-6 * rng.random(n),                                         # a few ulps apart
              np.r_[np.zeros(3000), 1.0 + 1e-3 * rng.random(n - 3000)]]           # zeros + narrow
-    for x in cases:
-        check(x, [0, n], W12)
+
+
+def test_adversarial():
+    for x in adversarial_cases():
+        check(x, [0, len(x)], W12)
 
 
 def test_narrow_large_intervals():
@@ -93,3 +95,37 @@ def test_synthesised_opacity_odf():
         o = od.odf(k, b, W12)
         rel = np.abs(g[s] - o) / (o + pl.kappa_c)
         assert rel.max() <= 1e-4 + (slack.max() / pl.kappa_c if slack.max() > 0 else 0)
+
+
+# ---- geometric means (exp of the sub-bin integral of ln kappa; a sub-bin reaching into zeros is 0)
+
+def test_geometric_random_lognormal_intervals():
+    rng = np.random.default_rng(11)
+    x = rng.lognormal(0, 5, (2, 100_003))
+    g = check(x, wl.equal_intervals(100_003, 7), W12, mean="geom")
+    assert np.all(np.diff(g, axis=2) >= 0)
+
+
+def test_geometric_adversarial():
+    for x in adversarial_cases():
+        check(x, [0, len(x)], W12, mean="geom")
+
+
+def test_geometric_small_ragged_and_zero_boundaries():
+    rng = np.random.default_rng(12)
+    x = rng.lognormal(0, 2, 1000)
+    x[rng.random(1000) < 0.3] = 0.0
+    for b in ([0, 1], [0, 5, 11, 12, 13, 40, 1000], [3, 997]):
+        check(x, b, W12, mean="geom")
+    check(x, [0, 1000], np.full(32, 1 / 32), mean="geom")
+    check(x, [0, 1000], [1.0], mean="geom")
+
+
+def test_geometric_below_arithmetic():
+    # AM-GM on every sub-bin of a positive array
+    rng = np.random.default_rng(13)
+    x = rng.lognormal(-3, 3, 50_000)
+    b = wl.equal_intervals(50_000, 4)
+    ga = gpu_odf(x, b, W12, "arith")
+    gg = check(x, b, W12, mean="geom")
+    assert np.all(gg <= ga * (1 + 1e-12))

@@ -23,6 +23,7 @@ def make_requests(w):
     n1, n2 = binding.grid_size(g1.lam0_nm, g1.lam1_nm, g1.R), binding.grid_size(g2.lam0_nm, g2.lam1_nm, g2.R)
     reqs.append(("odf", ([0, 1, 2, 3], g1, [0, 100, 500, n1], wl.ODF_WIDTHS_12)))
     reqs.append(("odf", ([3, 1], g2, [0, n2], [0.5, 0.3, 0.2])))
+    reqs.append(("odf", ([2, 0], g2, [0, 40, n2], wl.ODF_WIDTHS_12, binding.MEAN_GEOM)))
     return reqs
 
 
@@ -54,12 +55,13 @@ def test_alone_equals_in_the_mix_and_direct():
             ctx.synth_spectrum(a[0], a[1], a[2], a[3], MUS, o)
             direct.append(o.cpu().numpy())
         else:
-            sel, g, b, wd = a
+            sel, g, b, wd = a[:4]
+            mk = a[4] if len(a) > 4 else binding.MEAN_ARITH
             N = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
             k = torch.empty((len(sel), N), dtype=torch.float32, device="cuda")
             ctx.synth_opacity(g, sel, k)
             o = torch.empty((len(sel), len(b) - 1, len(wd)), dtype=torch.float64, device="cuda")
-            ctx.build_odf(k, b, wd, o)
+            ctx.build_odf(k, b, wd, o, mean_kind=mk)
             direct.append(o.cpu().numpy())
     torch.cuda.synchronize()
     srv = binding.Server(ctx, hbm_budget_bytes=8 << 30, max_inflight=1, rows_per_chunk=4)

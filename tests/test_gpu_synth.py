@@ -98,3 +98,20 @@ def test_full_size_sampled():
         lo, hi = sy.windows(pl)
         W = int(np.sum(np.maximum(hi - lo + 1, 0)))
         assert W <= evg[s] <= W + 8 * len(L)
+
+
+def test_precision_variants_against_oracle():
+    # the three library precisions on the same rows: all within the opacity tolerance; the
+    # all-FP64 variant within 1e-9 (outside the edge slack), compensated FP32 no worse than naive
+    w = wl.config_tiny(n_lines=400, lam=(300.0, 303.1), seed=8)
+    ctx, L = gpu_context(w)
+    sel = np.arange(4)
+    res = {p: gpu_synth(ctx, w, sel, precision=p)[0] for p in (0, 1, 2)}
+    for s in sel:
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        for p in (0, 1, 2):
+            bad, _, _ = opacity_violations(res[p][s], k, pl.kappa_c, slack)
+            assert len(bad) == 0, (p, s)
+        m = slack == 0
+        rel64 = np.abs(res[2][s][m].astype(np.float64) - k[m]) / (k[m] + pl.kappa_c)
+        assert rel64.max() < 1e-7        # FP32 output rounding bounds it

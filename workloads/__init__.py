@@ -158,6 +158,17 @@ def abundance_scales(n_comp: int, n_elements: int, seed: int) -> np.ndarray:
     return s
 
 
+def grey_atmosphere(D: int, Teff: float, logg: float, log_tau_top=-6.8, log_tau_bot=2.0, kappa_bar=0.1):
+    """Model-atmosphere input of the spectrum workload: D depths with tau log-spaced from
+    10^log_tau_top to 10^log_tau_bot, the grey Eddington law T = Teff (3/4 (tau + 2/3))^(1/4),
+    column mass m = tau / kappa_bar and hydrostatic pressure P = g m.  Returns (m, T, P)."""
+    tau = 10.0 ** np.linspace(log_tau_top, log_tau_bot, D)
+    T = Teff * (0.75 * (tau + 2.0 / 3.0)) ** 0.25
+    m = tau / kappa_bar
+    P = 10.0 ** logg * m
+    return m, T, P
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------
