@@ -35,11 +35,11 @@ import workloads as wl  # noqa: E402
 
 METRIC = "Voigt line-evals/s (line-by-line opacity synthesis + ODF binning)"
 UNIT = "line-evals/s"
-# FP32 operations of one far-wing profile evaluation (the tier that takes > 98% of
-# evaluations): v' = fma(G, sqrt2 kv B, sqrt2 kv E1); D = fma(v', v', 2a^2 - 1);
-# denominator fma(D, D, 8a^2); numerator fma(2sk, D, 4sk); accumulate fma(num, 1/den, sum):
-# 5 FFMA = 10 flop, plus one reciprocal on the special-function unit (not counted).
-FLOP_PER_EVAL = 10
+# FP32 operations of one far-wing profile evaluation in the paired rational form (the form
+# that takes most evaluations): v = fma(G, kv B, kv E1); D = fma(v, v, a^2 - 3/2); per pair
+# of points P = D0 D1 and sr = sk (1/P) (half an FMUL each), accumulate fma(sr, D_other, sum):
+# 3 FFMA + 1 FMUL = 7 flop, plus half a reciprocal on the special-function unit (not counted).
+FLOP_PER_EVAL = 7
 SMS = 152
 FP32_LANES_PER_SM = 128
 
@@ -598,8 +598,8 @@ def precision_arm(args):
         o = torch.empty((len(rows), 4, 12), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(len(rows)):       # one row per call: scratch is ~57 B per (row, line)
-            ctx.synth_opacity(g, rows[i:i + 1], k[i:i + 1], kc[i:i + 1], ev[i:i + 1],
+        for i in range(0, len(rows), 6):  # six rows per call: scratch is ~57 B per (row, line)
+            ctx.synth_opacity(g, rows[i:i + 6], k[i:i + 6], kc[i:i + 6], ev[i:i + 6],
                               opts=binding.make_opts(1e-3, 1e-2, prec))
         ctx.build_odf(k, b, wl.ODF_WIDTHS_12, o)
         torch.cuda.synchronize()

@@ -7,18 +7,20 @@
 // For an order statistic theta = x_(k): S(k) = sum_{x < theta} x + (k - #{x < theta}) theta.
 //
 // Order statistics: MSB radix multi-select on the FP32 bit patterns (values are
-// non-negative, so the bit order is the value order) over four levels of 11, 8, 8
-// and 4 bits (bits 30..20, 19..12, 11..4, 3..0).  Every histogram bin carries the
+// non-negative, so the bit order is the value order) over four levels of 12, 8, 8
+// and 3 bits (bits 30..19, 18..11, 10..3, 2..0).  Every histogram bin carries the
 // count (high 24 bits) and the sum of the bits below the bin's prefix (low 40
 // bits) in one 64-bit shared-memory atomic.  Values of one exponent E are integers
 // in units of 2^(max(E,1)-150), so every partial sum inside an exponent group is
 // exact integer arithmetic; only the sum across the 256 exponent groups is FP64.
 //
-// Passes over the interval: pass 1 (from HBM, 16-byte vector loads) builds the
-// level-1 histogram; pass 2 (from L2) copies the values that fall into a target's
-// level-1 bin into a shared-memory candidate buffer; levels 2-4 then run on that
-// buffer.  If the candidates do not fit, levels 2-4 re-read the interval instead.
-// Zeros are counted in registers and never enter atomics or the buffer.
+// Passes over the interval: pass 1 (from HBM) builds the level-1 histogram; pass 2
+// (from L2) copies the values that fall into a target's level-1 bin into a
+// shared-memory candidate buffer; levels 2-4 then run on that buffer.  If the
+// candidates do not fit, the next level re-reads the interval instead.  Each warp
+// reads 512 contiguous bytes per load; the 32 lanes of a warp aggregate their
+// histogram adds by bin (match + reduce) so that one atomic per distinct bin is
+// issued and no two lanes of a warp hit the same address.
 //
 // Geometric means (exp of the same integral of ln x) reuse the order statistics: one
 // more pass (from L2) sums ln x of the positive values between consecutive distinct
@@ -41,10 +43,15 @@ constexpr int kOdfThreads = 512;
 constexpr int kOdfWarps = kOdfThreads / 32;
 constexpr int kMaxSteps = 32;
 constexpr int kMaxTargets = kMaxSteps - 1;
-constexpr int kL1Bins = 2048;
-constexpr int kCand = 6144;                  // candidate buffer (32-bit patterns)
+constexpr int kL1Shift = 19;                       // level 1: bits 30..19
+constexpr int kL1Bins = 1 << (31 - kL1Shift);      // 4096
+constexpr int kL1PerGroup = 1 << (23 - kL1Shift);  // level-1 bins per exponent: 16
+constexpr int kMinSlots = 8;                       // h2 doubles as the 4096-int prefix array
+constexpr int kCand = 8192;                        // candidate buffer (32-bit patterns)
+constexpr long long kMaxInterval = 1ll << 21;      // count < 2^24 and low-bit sums < 2^40 per bin
 constexpr unsigned long long kOne = 1ull << 40;
 constexpr unsigned long long kLowMask = kOne - 1;
+constexpr unsigned kFull = 0xffffffffu;
 
 struct Target {
     long long k;                 // rank (0-based) of the order statistic
@@ -58,35 +65,62 @@ struct Target {
 
 __device__ __forceinline__ unsigned long long group_base(unsigned E) { return E >= 1 ? (1ull << 23) : 0ull; }
 
-// Visit every value of x[0..n) once.  Thread t walks a contiguous chunk of the
-// 16-byte-aligned body (so that runs of neighbouring grid points stay in one thread),
-// then the unaligned head and tail.  Every thread makes the same number of calls
-// f(bits, valid), so warp-wide votes inside f are safe.
-template <class F>
+// Visit every value of x[0..n) once.  The 16-byte-aligned body is read as float4 with
+// U loads in flight per lane before any is consumed, in one of two layouts:
+//  * CHUNKED: thread t walks one contiguous chunk, so runs of neighbouring grid points
+//    (which usually share a histogram bin) stay in one thread and merge in registers,
+//    while the lanes of a warp sit far apart and rarely hit the same bin;
+//  * otherwise warp-coalesced: each warp owns a contiguous range and lane l reads float4
+//    l, l+32, ... of it (512 contiguous bytes per warp and load).
+// The unaligned head and tail (< 4 values each) go to threads 0..3.  Every lane of a
+// warp makes the same number of calls f(bits, valid), so warp-wide collectives inside f
+// are safe.
+template <bool CHUNKED, class F>
 __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long long n, F&& f) {
-    constexpr int U = 4;   // 16-byte loads in flight per thread before any of them is consumed
-    const int tid = threadIdx.x;
+    constexpr int U = 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
     long long head = mis ? (long long)(4u - mis) : 0;
     if (head > n) head = n;
     const float4* body = reinterpret_cast<const float4*>(x + head);
     const long long nv = (n - head) >> 2;
-    const long long per = (nv + kOdfThreads - 1) / kOdfThreads;
-    const long long i0 = (long long)tid * per;
-    for (long long it = 0; it < per; it += U) {
-        float4 q[U];
+    if (CHUNKED) {
+        const long long per = (nv + kOdfThreads - 1) / kOdfThreads;
+        const long long i0 = (long long)tid * per;
+        for (long long it = 0; it < per; it += U) {
+            float4 q[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long long i = i0 + it + u;
-            q[u] = (it + u < per && i < nv) ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < U; ++u) {
+                const long long i = i0 + it + u;
+                q[u] = (it + u < per && i < nv) ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool v = (it + u < per) && (i0 + it + u < nv);
+                f(__float_as_uint(q[u].x), v);
+                f(__float_as_uint(q[u].y), v);
+                f(__float_as_uint(q[u].z), v);
+                f(__float_as_uint(q[u].w), v);
+            }
         }
+    } else {
+        const long long per = (((nv + kOdfWarps - 1) / kOdfWarps) + 31) & ~31ll;   // float4 per warp
+        const long long w0 = (long long)warp * per, w1 = min(w0 + per, nv);
+        for (long long it = w0; it < w0 + per; it += 32 * U) {
+            float4 q[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const bool v = (it + u < per) && (i0 + it + u < nv);
-            f(__float_as_uint(q[u].x), v);
-            f(__float_as_uint(q[u].y), v);
-            f(__float_as_uint(q[u].z), v);
-            f(__float_as_uint(q[u].w), v);
+            for (int u = 0; u < U; ++u) {
+                const long long i = it + 32 * u + lane;
+                q[u] = i < w1 ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool v = it + 32 * u + lane < w1;
+                f(__float_as_uint(q[u].x), v);
+                f(__float_as_uint(q[u].y), v);
+                f(__float_as_uint(q[u].z), v);
+                f(__float_as_uint(q[u].w), v);
+            }
         }
     }
     const long long t0 = head + (nv << 2);
@@ -94,8 +128,38 @@ __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long
     f(t0 + tid < n ? __float_as_uint(__ldg(x + t0 + tid)) : 0u, t0 + tid < n);
 }
 
-// Per-thread run merging of histogram adds: consecutive values of a thread's chunk
-// usually fall into the same bin; they are summed in registers and one shared-memory
+// Histogram add of one value per lane (count in the high 24 bits, low bits below the
+// bin's prefix in the low 40).  Called by all 32 lanes; key < 0 adds nothing.
+//   ODF_AGG 0: one atomic per lane;
+//   ODF_AGG 1: when every lane of the warp has the same key (smooth stretches of an
+//              opacity array), one atomic for the warp with the reduced low-bit sum
+//              (each low part < 2^19, so 32 of them fit 32 bits), else one per lane;
+//   ODF_AGG 2: lanes with equal keys aggregated by match + reduce, one atomic per key.
+#ifndef ODF_AGG
+#define ODF_AGG 1
+#endif
+__device__ __forceinline__ void agg_add(unsigned long long* __restrict__ h, int key, unsigned low, int lane) {
+#if ODF_AGG == 2
+    const unsigned peers = __match_any_sync(kFull, key);
+    const unsigned sum = __reduce_add_sync(peers, low);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], ((unsigned long long)__popc(peers) << 40) + sum);
+#elif ODF_AGG == 1
+    const int kmin = __reduce_min_sync(kFull, key), kmax = __reduce_max_sync(kFull, key);
+    if (kmin == kmax) {
+        if (kmin >= 0) {
+            const unsigned sum = __reduce_add_sync(kFull, low);
+            if (lane == 0) atomicAdd(&h[kmin], (32ull << 40) + sum);
+        }
+    } else if (key >= 0) {
+        atomicAdd(&h[key], kOne + low);
+    }
+#else
+    if (key >= 0) atomicAdd(&h[key], kOne + low);
+#endif
+}
+
+// Per-thread run merging of histogram adds (CHUNKED passes): consecutive values of a
+// thread's chunk that fall into the same bin are summed in registers and one shared-memory
 // atomic is issued per run.
 struct RunAdd {
     int key = -1;
@@ -115,6 +179,21 @@ struct RunAdd {
         val = 0;
     }
 };
+
+// Warp-aggregated append to the candidate buffer (one shared atomic per warp and call).
+__device__ __forceinline__ void agg_append(unsigned* __restrict__ cand, int* n_cand, bool take, unsigned bits,
+                                           int lane) {
+    const unsigned m = __ballot_sync(kFull, take);
+    if (m == 0u) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(n_cand, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (take) {
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        if (pos < kCand) cand[pos] = bits;
+    }
+}
 
 // Run merging of FP64 sums into a shared-memory array (geometric pass).
 struct RunAddF64 {
@@ -170,12 +249,12 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
     }
     long long incl = cnt;
     for (int d = 1; d < 32; d <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, incl, d);
+        long long y = __shfl_up_sync(kFull, incl, d);
         if (lane >= d) incl += y;
     }
     const long long before = incl - cnt + t.cnt_lt;
     const bool mine = cnt > 0 && (t.k >= before) && (t.k < before + cnt);
-    const unsigned owner = __ballot_sync(0xffffffffu, mine);
+    const unsigned owner = __ballot_sync(kFull, mine);
     const int ow = owner ? __ffs(owner) - 1 : 31;
     unsigned long long ivs = 0;
     long long cnt_below = 0;
@@ -197,9 +276,9 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
         }
         cnt_below = run;
     }
-    for (int d = 16; d > 0; d >>= 1) ivs += __shfl_down_sync(0xffffffffu, ivs, d);
-    found = __shfl_sync(0xffffffffu, found, ow);
-    cnt_below = __shfl_sync(0xffffffffu, cnt_below, ow);
+    for (int d = 16; d > 0; d >>= 1) ivs += __shfl_down_sync(kFull, ivs, d);
+    found = __shfl_sync(kFull, found, ow);
+    cnt_below = __shfl_sync(kFull, cnt_below, ow);
     if (lane == 0) {
         t.iv_lt += ivs;
         t.cnt_lt = cnt_below;
@@ -214,19 +293,20 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
                                                      double* __restrict__ out, int geom) {
     extern __shared__ unsigned long long sm[];
     const int nt = n_steps - 1;
-    const int nslots = nt > 4 ? nt : 4;
-    unsigned long long* h1 = sm;                             // [2048]
-    unsigned long long* h2 = sm + kL1Bins;                   // [nslots][256]; its first 8 KB double as cbefore
-    int* cbefore = reinterpret_cast<int*>(h2);               // [2048] (only before the levels)
+    const int nslots = nt > kMinSlots ? nt : kMinSlots;
+    unsigned long long* h1 = sm;                             // [4096]
+    unsigned long long* h2 = sm + kL1Bins;                   // [nslots][256]; first 16 KB double as cincl
+    int* cincl = reinterpret_cast<int*>(h2);                 // [4096] inclusive prefix counts (before the levels)
     unsigned* cand = reinterpret_cast<unsigned*>(h2 + (size_t)nslots * 256);   // [kCand]
-    short* slot2 = reinterpret_cast<short*>(cand + kCand);   // [nslots][256]: depth-19 prefix -> slot
-    __shared__ short slot1[kL1Bins];
+    short* slot1 = reinterpret_cast<short*>(cand + kCand);   // [4096]: level-1 bin -> slot
+    short* slot2 = slot1 + kL1Bins;                          // [nslots][256]: 20-bit prefix -> slot
+    __shared__ unsigned tbits[kL1Bins / 32];                 // bitmap of the targets' level-1 bins
     __shared__ unsigned long long gsum[256];
     __shared__ double gpre[257];
     __shared__ Target tg[kMaxTargets];
     __shared__ unsigned dpre[kMaxTargets];
     __shared__ int n_distinct, n_cand;
-    __shared__ long long s_zero;
+    __shared__ unsigned s_zero;
     __shared__ int wtot[kOdfWarps];
     __shared__ unsigned thr[kMaxTargets];       // geometric pass: distinct order statistics, ascending
     __shared__ double lsum[kMaxTargets + 1];    // geometric pass: inclusive prefix sums of ln x per bucket
@@ -239,34 +319,33 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (int i = tid; i < kL1Bins; i += kOdfThreads) { h1[i] = 0ull; slot1[i] = -1; }
-    if (tid == 0) { s_zero = 0; n_cand = 0; }
+    if (tid < kL1Bins / 32) tbits[tid] = 0u;
+    if (tid == 0) { s_zero = 0u; n_cand = 0; }
     __syncthreads();
 
-    // ---- pass 1 (HBM): level-1 histogram with exact low-bit sums
-    long long zeros = 0;
+    // ---- pass 1 (HBM): level-1 histogram with exact low-bit sums (zeros land in bin 0)
     {
+        unsigned zeros = 0;
         RunAdd run;
-        for_each_value(x, n, [&](unsigned bits, bool valid) {
+        for_each_value<true>(x, n, [&](unsigned bits, bool valid) {
             if (!valid) return;
             bits &= 0x7fffffffu;
-            if (bits == 0u) { ++zeros; return; }
-            run.add(h1, (int)(bits >> 20), kOne | (unsigned long long)(bits & 0xfffffu));
+            zeros += bits == 0u ? 1u : 0u;
+            run.add(h1, (int)(bits >> kL1Shift), kOne | (unsigned long long)(bits & ((1u << kL1Shift) - 1u)));
         });
         run.flush(h1);
+        zeros = __reduce_add_sync(kFull, zeros);
+        if (lane == 0 && zeros) atomicAdd(&s_zero, zeros);
     }
-    for (int d = 16; d > 0; d >>= 1) zeros += __shfl_down_sync(0xffffffffu, zeros, d);
-    if (lane == 0 && zeros) atomicAdd((unsigned long long*)&s_zero, (unsigned long long)zeros);
-    __syncthreads();
-    if (tid == 0) h1[0] += (unsigned long long)s_zero << 40;
     __syncthreads();
 
-    // ---- exclusive scan of the level-1 counts (4 bins per thread)
+    // ---- inclusive scan of the level-1 counts (8 bins per thread)
     {
-        int c[4], v = 0;
-        for (int m = 0; m < 4; ++m) { c[m] = (int)(h1[4 * tid + m] >> 40); v += c[m]; }
+        int c[8], v = 0;
+        for (int m = 0; m < 8; ++m) { c[m] = (int)(h1[8 * tid + m] >> 40); v += c[m]; }
         int incl = v;
         for (int d = 1; d < 32; d <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, d);
+            int y = __shfl_up_sync(kFull, incl, d);
             if (lane >= d) incl += y;
         }
         if (lane == 31) wtot[warp] = incl;
@@ -274,34 +353,22 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         if (warp == 0) {
             int t = lane < kOdfWarps ? wtot[lane] : 0, ti = t;
             for (int d = 1; d < 32; d <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, ti, d);
+                int y = __shfl_up_sync(kFull, ti, d);
                 if (lane >= d) ti += y;
             }
             if (lane < kOdfWarps) wtot[lane] = ti - t;
         }
         __syncthreads();
-        int ex = wtot[warp] + incl - v;
-        for (int m = 0; m < 4; ++m) { cbefore[4 * tid + m] = ex; ex += c[m]; }
+        int run = wtot[warp] + incl - v;
+        for (int m = 0; m < 8; ++m) { run += c[m]; cincl[8 * tid + m] = run; }
     }
     if (tid < 256) {
         unsigned long long acc = 0;
-        for (int m = 0; m < 8; ++m) {
-            const unsigned long long h = h1[tid * 8 + m];
-            acc += (h >> 40) * (group_base(tid) + ((unsigned long long)m << 20)) + (h & kLowMask);
+        for (int m = 0; m < kL1PerGroup; ++m) {
+            const unsigned long long h = h1[tid * kL1PerGroup + m];
+            acc += (h >> 40) * (group_base(tid) + ((unsigned long long)m << kL1Shift)) + (h & kLowMask);
         }
         gsum[tid] = acc;
-    }
-    if (tid < nt) {
-        Target t;
-        // u = c_s n rounded to FP64 exactly as written (no fused multiply-add), as the reference does
-        t.k = (long long)floor(__dmul_rn(cw[tid + 1], (double)n));
-        t.total = t.k >= n;
-        t.slot = -1;
-        t.prefix = 0;
-        t.cnt_lt = 0;
-        t.cnt_in = 0;
-        t.iv_lt = 0;
-        tg[tid] = t;
     }
     __syncthreads();
     if (warp == 0) {
@@ -315,7 +382,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         }
         double incl = tot;
         for (int d = 1; d < 32; d <<= 1) {
-            double y = __shfl_up_sync(0xffffffffu, incl, d);
+            double y = __shfl_up_sync(kFull, incl, d);
             if (lane >= d) incl += y;
         }
         double run = incl - tot;
@@ -324,34 +391,49 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             run += loc[m];
         }
         if (lane == 31) gpre[256] = run;
-    }
-    // each target's level-1 bin (the thread owning that bin records it)
-    for (int t = 0; t < nt; ++t) {
-        if (tg[t].total) continue;
-        const long long kk = tg[t].k;
-        for (int bb = 4 * tid; bb < 4 * tid + 4; ++bb) {
-            const long long c = (long long)(h1[bb] >> 40);
-            if (c > 0 && cbefore[bb] <= kk && kk < cbefore[bb] + c) {
-                tg[t].prefix = (unsigned)bb << 20;
-                tg[t].cnt_lt = cbefore[bb];
-                tg[t].cnt_in = c;
-                unsigned long long acc = 0;
-                for (int m = bb & ~7; m < bb; ++m) {
-                    const unsigned long long h = h1[m];
-                    acc += (h >> 40) * (group_base(bb >> 3) + ((unsigned long long)(m & 7) << 20)) + (h & kLowMask);
-                }
-                tg[t].iv_lt = acc;
+    } else if (warp == 1 && lane < nt) {
+        // each target's level-1 bin: the first bin whose inclusive count exceeds its rank
+        Target t;
+        // u = c_s n rounded to FP64 exactly as written (no fused multiply-add), as the reference does
+        t.k = (long long)floor(__dmul_rn(cw[lane + 1], (double)n));
+        t.total = t.k >= n;
+        t.slot = -1;
+        t.prefix = 0;
+        t.cnt_lt = 0;
+        t.cnt_in = 0;
+        t.iv_lt = 0;
+        if (!t.total) {
+            int lo = 0, hi = kL1Bins - 1;   // smallest bb with cincl[bb] > k
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((long long)cincl[mid] > t.k) hi = mid;
+                else lo = mid + 1;
             }
+            const int bb = lo;
+            const long long cnt = (long long)(h1[bb] >> 40);
+            t.prefix = (unsigned)bb << kL1Shift;
+            t.cnt_lt = (long long)cincl[bb] - cnt;
+            t.cnt_in = cnt;
+            unsigned long long acc = 0;
+            const unsigned E = (unsigned)bb / kL1PerGroup;
+            for (int m = bb & ~(kL1PerGroup - 1); m < bb; ++m) {
+                const unsigned long long h = h1[m];
+                acc += (h >> 40) * (group_base(E) + ((unsigned long long)(m & (kL1PerGroup - 1)) << kL1Shift)) +
+                       (h & kLowMask);
+            }
+            t.iv_lt = acc;
         }
+        tg[lane] = t;
     }
     __syncthreads();
+
     // ---- levels 2..4.  The counts of the current target prefixes are known from the last
     // histogram; once they fit the candidate buffer, one pass (from L2) collects those
     // values and every remaining level runs on the buffer.  Until then each level is a
     // histogram pass over the interval (from L2) restricted to the target prefixes, found
-    // with O(1) prefix -> slot tables (slot1 at 11 resolved bits, slot2 at 19).
-    const int shifts[3] = {12, 4, 0};
-    const int widths[3] = {8, 8, 4};
+    // with O(1) prefix -> slot tables (slot1 at 12 resolved bits, slot2 at 20).
+    const int shifts[3] = {11, 3, 0};
+    const int widths[3] = {8, 8, 3};
     bool have_cand = false;
     int nc = 0;
     int nd_prev = 0;
@@ -359,23 +441,27 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         const int sh = shifts[lvl], wb = widths[lvl];
         const int hiShift = sh + wb;
         const int nbins = 1 << wb;
-        if (tid == 0) {
-            int nd = 0;
-            long long tot_in = 0;
-            for (int t = 0; t < nt; ++t) {
-                if (tg[t].total) continue;
-                int f = -1;
-                for (int q = 0; q < nd; ++q)
-                    if (dpre[q] == tg[t].prefix) f = q;
-                if (f < 0) {
-                    dpre[nd] = tg[t].prefix;
-                    f = nd++;
-                    tot_in += tg[t].cnt_in - (tg[t].prefix == 0u ? s_zero : 0);
-                }
-                tg[t].slot = f;
+        if (warp == 0) {
+            // distinct target prefixes -> slots (lane t holds target t)
+            const bool act = lane < nt && !tg[lane].total;
+            const unsigned p = act ? tg[lane].prefix : 0xffffffffu;
+            const unsigned grp = __match_any_sync(kFull, p);
+            const int first = __ffs(grp) - 1;
+            const bool leader = act && first == lane;
+            const unsigned lm = __ballot_sync(kFull, leader);
+            const int slot = __popc(lm & ((1u << first) - 1u));
+            if (act) tg[lane].slot = slot;
+            long long in = 0;
+            if (leader) {
+                dpre[slot] = p;
+                in = tg[lane].cnt_in - (p == 0u ? (long long)s_zero : 0ll);
+                if (lvl == 0) atomicOr(&tbits[p >> (kL1Shift + 5)], 1u << ((p >> kL1Shift) & 31u));
             }
-            n_distinct = nd;
-            n_cand = (!have_cand && tot_in <= kCand) ? 0 : -1;   // 0: collect in this level
+            for (int d = 16; d > 0; d >>= 1) in += __shfl_down_sync(kFull, in, d);
+            if (lane == 0) {
+                n_distinct = __popc(lm);
+                n_cand = (!have_cand && in <= kCand) ? 0 : -1;   // 0: collect in this level
+            }
         }
         __syncthreads();
         const int nd = n_distinct;
@@ -383,24 +469,24 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         const bool collect = n_cand == 0;
         // prefix -> slot tables for the current depth
         if (lvl == 0) {
-            for (int q = tid; q < nd; q += kOdfThreads) slot1[dpre[q] >> 20] = (short)q;
+            for (int q = tid; q < nd; q += kOdfThreads) slot1[dpre[q] >> kL1Shift] = (short)q;
         } else if (lvl == 1) {
             for (int i = tid; i < nd_prev * 256; i += kOdfThreads) slot2[i] = -1;
         }
         __syncthreads();
         if (lvl == 1)
             for (int q = tid; q < nd; q += kOdfThreads) {
-                const int q1 = slot1[dpre[q] >> 20];
-                if (q1 >= 0) slot2[q1 * 256 + ((dpre[q] >> 12) & 255u)] = (short)q;
+                const int q1 = slot1[dpre[q] >> kL1Shift];
+                if (q1 >= 0) slot2[q1 * 256 + ((dpre[q] >> 11) & 255u)] = (short)q;
             }
         for (int i = tid; i < nd * 256; i += kOdfThreads) h2[i] = 0ull;
         __syncthreads();
         // slot of a value at the current depth, or -1 (zeros are never in a slot)
         auto slot_of = [&](unsigned bits) -> int {
             if (bits == 0u) return -1;
-            const int q1 = slot1[bits >> 20];
+            const int q1 = slot1[bits >> kL1Shift];
             if (q1 < 0 || lvl == 0) return q1;
-            if (lvl == 1) return slot2[q1 * 256 + ((bits >> 12) & 255u)];
+            if (lvl == 1) return slot2[q1 * 256 + ((bits >> 11) & 255u)];
             const unsigned pre = (bits >> hiShift) << hiShift;
             int q = -1;
             for (int r = 0; r < nd; ++r)
@@ -408,37 +494,35 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             return q;
         };
         if (collect) {
-            // warp-aggregated append: one shared atomic per warp and call
-            for_each_value(x, n, [&](unsigned bits, bool valid) {
-                bits &= 0x7fffffffu;
-                const bool take = valid && slot_of(bits) >= 0;
-                const unsigned m = __ballot_sync(0xffffffffu, take);
-                if (m == 0u) return;
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&n_cand, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (take) {
-                    const int pos = base + __popc(m & ((1u << lane) - 1u));
-                    if (pos < kCand) cand[pos] = bits;
-                }
-            });
+            if (lvl == 0) {
+                for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
+                    bits &= 0x7fffffffu;
+                    const bool take =
+                        valid && bits != 0u && ((tbits[bits >> (kL1Shift + 5)] >> ((bits >> kL1Shift) & 31u)) & 1u);
+                    agg_append(cand, &n_cand, take, bits, lane);
+                });
+            } else {
+                for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
+                    bits &= 0x7fffffffu;
+                    agg_append(cand, &n_cand, valid && slot_of(bits) >= 0, bits, lane);
+                });
+            }
             __syncthreads();
             nc = min(n_cand, kCand);
             have_cand = true;
         }
         if (have_cand) {
-            for (int i = tid; i < nc; i += kOdfThreads) {
-                const unsigned bits = cand[i];
-                const int q = slot_of(bits);
-                if (q < 0) continue;
+            for (int i0 = 0; i0 < nc; i0 += kOdfThreads) {
+                const int i = i0 + tid;
+                const unsigned bits = i < nc ? cand[i] : 0u;
+                const int q = i < nc ? slot_of(bits) : -1;
                 const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
-                const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
-                atomicAdd(&h2[q * 256 + sub], kOne | low);
+                const unsigned low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
+                agg_add(h2, q >= 0 ? q * 256 + (int)sub : -1, low, lane);
             }
         } else {
             RunAdd run;
-            for_each_value(x, n, [&](unsigned bits, bool valid) {
+            for_each_value<true>(x, n, [&](unsigned bits, bool valid) {
                 bits &= 0x7fffffffu;
                 const int q = valid ? slot_of(bits) : -1;
                 if (q < 0) return;
@@ -481,7 +565,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         const int m = n_thr;
         // bucket of x = number of order statistics <= x; values below thr[j] sit in buckets 0..j
         RunAddF64 run;
-        for_each_value(x, n, [&](unsigned bits, bool valid) {
+        for_each_value<true>(x, n, [&](unsigned bits, bool valid) {
             bits &= 0x7fffffffu;
             if (!valid || bits == 0u) return;
             int b = 0;
@@ -535,9 +619,9 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
 
 size_t odf_smem_bytes(int n_steps) {
     const int nt = n_steps - 1;
-    const int nslots = nt > 4 ? nt : 4;
+    const int nslots = nt > kMinSlots ? nt : kMinSlots;
     return (kL1Bins + (size_t)nslots * 256) * sizeof(unsigned long long) + kCand * sizeof(unsigned) +
-           (size_t)nslots * 256 * sizeof(short);
+           (kL1Bins + (size_t)nslots * 256) * sizeof(short);
 }
 
 }  // namespace
@@ -558,7 +642,7 @@ int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, 
     for (int k = 0; k < K; ++k) {
         const int64_t len = bounds[k + 1] - bounds[k];
         if (len < 1) return fail(MPSA_EINVAL, "build_odf: bounds not strictly increasing at %d", k);
-        if (len >= (1 << 21)) return fail(MPSA_EINVAL, "build_odf: interval %d has %lld points (max 2^21-1)", k, (long long)len);
+        if (len >= kMaxInterval) return fail(MPSA_EINVAL, "build_odf: interval %d has %lld points (max 2^21-1)", k, (long long)len);
     }
     // cumulative widths: FP64 left-to-right partial sums, the last forced to 1
     double acc = 0.0;
@@ -675,7 +759,7 @@ extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_r
     for (int k = 0; k < K; ++k) {
         const int64_t len = bounds[k + 1] - bounds[k];
         if (len < 1) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds not strictly increasing at %d", k);
-        if (len >= (1 << 21))
+        if (len >= kMaxInterval)
             return fail(MPSA_EINVAL, "build_odf_noalloc: interval %d has %lld points (max 2^21-1)", k, (long long)len);
     }
     double cw[kMaxSteps + 1];

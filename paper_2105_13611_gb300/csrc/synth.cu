@@ -286,10 +286,19 @@ __global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const
         float a = av[q];
         float srel = 0.f;
         int jlo = 1, jhi = 0, ilo = 1, ihi = 0;
-        if (lnk0[q] >= ltp) {
-            const float rel = fminf(lnS[q] - ltp, 88.f);
+        bool reach = lnk0[q] >= ltp;
+        const float rel = fminf(lnS[q] - ltp, 88.f);
+        const float r = expf(-rel);
+        if (reach) {
+            // cheap cull before the crossing search: H(v, a) <= 4a/(sqrt(pi) v^2) + exp(-v^2/4)
+            // (the convolution split at |t| = v/2), so the line stays below the cut beyond vb;
+            // lines whose bound window misses the grid (narrow grids) are dropped here
+            const float vb = fmaxf(sqrtf(8.f * kInvSqrtPi * a / r), 2.f * sqrtf(fmaxf(logf(2.f / r), 0.f))) + 1.f;
+            const float hb = fminf(f + d_red(vb, kv, lnq), 1.0e9f), lb = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f);
+            reach = (double)c + (double)hb + 2.0 >= 0.0 && (double)c + (double)lb - 2.0 <= (double)(N - 1);
+        }
+        if (reach) {
             srel = expf(rel);
-            const float r = expf(-rel);
             float vo, vi;
             cut_speeds(a, r, &vo, &vi);
             const float vo2 = vo * (1.f + 1e-5f);
@@ -479,32 +488,49 @@ struct NearRec {
 //    p = {sqrt2 kv B, sqrt2 kv E1, 2a^2 - 1, 8a^2}, q = {2 sk, 4 sk} for both.
 // The PTS points are evaluated without branches so that their dependency chains
 // interleave; MASKED lines (partial coverage or points near the cut) select with a mask.
-constexpr int kFarRat = 0, kFarExact = 1, kFarY = 2;
+//  * kFarRatPair: the rational form with one reciprocal for two points,
+//    r = 1/(D_0 D_1), sk/D_0 = (sk r) D_1 and sk/D_1 = (sk r) D_0 (relative error about
+//    two ulps); per evaluation 4 FP32 instructions and half a reciprocal.  Used where
+//    |v| < 1e9 on the whole tile, so that D_0 D_1 < 1e36 stays finite.
+constexpr int kFarRat = 0, kFarExact = 1, kFarY = 2, kFarRatPair = 3;
+
 template <int PTS, int FORM, bool MASKED>
 __device__ __forceinline__ void far_line(const float4 p, const float2 q, int klo, int khi, bool chk,
                                          const float (&G)[PTS], float (&part)[PTS]) {
+    if constexpr (FORM == kFarRatPair) {
+        static_assert(PTS % 2 == 0 && !MASKED, "paired form: plain lines, even point count");
 #pragma unroll
-    for (int k = 0; k < PTS; ++k) {
-        const float vp = fmaf(G[k], p.x, p.y);
-        const float D = fmaf(vp, vp, p.z);
-        float t, y;
-        if (FORM == kFarRat) {
-            y = rcp_approx(D);
-            t = p.w;
-        } else if (FORM == kFarY) {
-            y = rcp_approx(D);
-            t = fmaf(q.y, y, q.x);
-        } else {
-            y = rcp_approx(fmaf(D, D, p.w));
-            t = fmaf(q.x, D, q.y);
+        for (int k = 0; k < PTS; k += 2) {
+            const float v0 = fmaf(G[k], p.x, p.y), v1 = fmaf(G[k + 1], p.x, p.y);
+            const float D0 = fmaf(v0, v0, p.z), D1 = fmaf(v1, v1, p.z);
+            const float sr = p.w * rcp_approx(D0 * D1);
+            part[k] = fmaf(sr, D1, part[k]);
+            part[k + 1] = fmaf(sr, D0, part[k + 1]);
         }
-        if (MASKED) {
-            const float l = t * y;
-            bool ok = (k >= klo) & (k <= khi);
-            if (chk) ok = ok & (l >= 1.f);
-            part[k] += ok ? l : 0.f;
-        } else {
-            part[k] = fmaf(t, y, part[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < PTS; ++k) {
+            const float vp = fmaf(G[k], p.x, p.y);
+            const float D = fmaf(vp, vp, p.z);
+            float t, y;
+            if (FORM == kFarRat) {
+                y = rcp_approx(D);
+                t = p.w;
+            } else if (FORM == kFarY) {
+                y = rcp_approx(D);
+                t = fmaf(q.y, y, q.x);
+            } else {
+                y = rcp_approx(fmaf(D, D, p.w));
+                t = fmaf(q.x, D, q.y);
+            }
+            if (MASKED) {
+                const float l = t * y;
+                bool ok = (k >= klo) & (k <= khi);
+                if (chk) ok = ok & (l >= 1.f);
+                part[k] += ok ? l : 0.f;
+            } else {
+                part[k] = fmaf(t, y, part[k]);
+            }
         }
     }
 }
@@ -607,7 +633,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                         const float zmin2 = fmaf(vmin, vmin, A);
                         if (zmin2 * zmin2 >= 1.0e6f * fmaf(2.f, A, 2.f)) {
                             fa = make_float4(kv * B, kv * E1, A - 1.5f, sk);
-                            fb = make_float4(0.f, 0.f, __int_as_float(flags | kFlRat), 0.f);
+                            fb = make_float4(0.f, 0.f, __int_as_float(flags | kFlRat | (yform ? kFlAlt : 0)), 0.f);
                         } else {
                             fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
                             fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
@@ -636,7 +662,8 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
             if (isFar) {
                 const int fl = __float_as_int(fb.z);
                 const bool plain = (fl & kFlFull) && !(fl & kFlChk);
-                cat = plain ? ((fl & kFlRat) ? 0 : ((fl & kFlAlt) ? 2 : 1)) : 3;
+                // rational lines with |v| >= 1e9 somewhere take the single-reciprocal masked path
+                cat = plain ? ((fl & kFlRat) ? ((fl & kFlAlt) ? 3 : 0) : ((fl & kFlAlt) ? 2 : 1)) : 3;
             } else if (isNear) {
                 cat = 4;
             }
@@ -676,7 +703,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
             {
                 int r = 0;
                 for (; r < tot[0]; ++r)
-                    far_line<PTS, kFarRat, false>(sFarA[r], make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                    far_line<PTS, kFarRatPair, false>(sFarA[r], make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
                 for (; r < tot[0] + tot[1]; ++r) {
                     const float4 q4 = sFarB[r];
                     far_line<PTS, kFarExact, false>(sFarA[r], make_float2(q4.x, q4.y), 0, PTS - 1, false, G, part);
@@ -833,13 +860,17 @@ struct Tile64Args {
     double lam0_nm, lnq64;
 };
 
+// All-FP64 variant: one point per thread (256-point tiles, so that narrow grids still fill
+// the GPU), line constants in FP64 per (line, tile), FP64 Voigt tiers.
+constexpr int kTile64 = 256;
 __global__ void __launch_bounds__(256) k_tiles64(Tile64Args g) {
-    constexpr int THREADS = 256, PTS = kPtsPerThread, TILE = THREADS * PTS;
+    constexpr int THREADS = 256, PTS = 1, TILE = THREADS * PTS;
+    static_assert(TILE == kTile64, "FP64 tile size");
     __shared__ double sS[THREADS], sA[THREADS], sNu[THREADS], sDnu[THREADS];
     __shared__ int sLo[THREADS], sHi[THREADS];
     __shared__ int sN;
     const int s = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
-    const RowDesc r = row_desc(g.t, s, kTile);
+    const RowDesc r = row_desc(g.t, s, kTile64);
     const int J0 = tile * TILE;
     const double* row = g.pop + (size_t)g.sel[s] * g.pop_stride_;
     const double T = row[kPopT], ne = row[kPopNe], nHI = row[kPopNHI], rho = row[kPopRho];
@@ -880,7 +911,7 @@ __global__ void __launch_bounds__(256) k_tiles64(Tile64Args g) {
                     sS[slot] = S;
                     sA[slot] = gam / (4.0 * kPI * dnu);
                     sNu[slot] = nu0;
-                    sDnu[slot] = dnu;
+                    sDnu[slot] = 1.0 / dnu;
                     sLo[slot] = jlo;
                     sHi[slot] = jhi;
                 }
@@ -888,12 +919,12 @@ __global__ void __launch_bounds__(256) k_tiles64(Tile64Args g) {
             __syncthreads();
             const int n = sN;
             for (int i = 0; i < n; ++i) {
-                const double S = sS[i], a = sA[i], nu0 = sNu[i], dnu = sDnu[i];
+                const double S = sS[i], a = sA[i], nu0 = sNu[i], inv_dnu = sDnu[i];
                 const int lo = sLo[i], hi = sHi[i];
                 for (int k = 0; k < PTS; ++k) {
                     const int j = J0 + k * THREADS + tid;
                     if (j < lo || j > hi) continue;
-                    const double l = S * voigt_H64((nu[k] - nu0) / dnu, a);
+                    const double l = S * voigt_H64((nu[k] - nu0) * inv_dnu, a);
                     if (l >= tp) acc[k] += l;
                 }
             }
@@ -1037,7 +1068,8 @@ int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, do
     Scratch sc(st);
     PrepBufs b;
     int r;
-    if ((r = prep_alloc(b, ctx, n_sel, N, R, kTile, [&](auto** p, size_t n) { return sc.alloc(p, n); }))) return r;
+    const int tile = prec == MPSA_PREC_FP64 ? kTile64 : kTile;
+    if ((r = prep_alloc(b, ctx, n_sel, N, R, tile, [&](auto** p, size_t n) { return sc.alloc(p, n); }))) return r;
     if ((r = prep_launch(b, ctx, pop, d_sel, lam0_nm, kc_out, evals, opts, st))) return r;
     const TileArgs ta = tile_args(b, kappa);
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);

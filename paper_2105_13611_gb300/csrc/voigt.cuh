@@ -162,15 +162,21 @@ __device__ inline double voigt_H64(double v, double a) {
     v = fabs(v);
     const double Z = v * v + a * a;
     if (Z >= 36.0) {
-        double tr = v, ti = a;
+        // continued fraction t <- z - (k/2)/t, bottom-up, with t = P/Q kept as a fraction
+        // (P, Q) <- (z P - (k/2) Q, P) so that only the final step divides; H = Re(i Q/P)/sqrt(pi).
+        // |P| grows like |z|^(levels+1), far inside the FP64 range for any grid.
         const int levels = Z >= 1600.0 ? 4 : 16;   // 4 levels reach 1e-14 for |z| >= 40
+        double pr = v, pi = a, qr = 1.0, qi = 0.0;
         for (int k = levels; k >= 1; --k) {
-            const double m = 0.5 * k / (tr * tr + ti * ti);
-            const double ntr = v - m * tr;
-            ti = a + m * ti;
-            tr = ntr;
+            const double c = 0.5 * k;
+            const double npr = fma(-c, qr, fma(v, pr, -a * pi));
+            const double npi = fma(-c, qi, fma(v, pi, a * pr));
+            qr = pr;
+            qi = pi;
+            pr = npr;
+            pi = npi;
         }
-        double h = ti / (1.7724538509055160273 * (tr * tr + ti * ti));
+        double h = (qr * pi - qi * pr) / (1.7724538509055160273 * fma(pr, pr, pi * pi));
         if (a < 1e-2) h += exp(a * a - v * v) * cos(2.0 * v * a);
         return h;
     }
