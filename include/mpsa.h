@@ -177,7 +177,7 @@ int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const in
  *     width, the paper's default in Sect. 2.3; a sub-bin whose rank range
  *     reaches into zero values has geometric mean 0).
  *   odf_out (device, double[n_rows][K][n_steps]).
- * Order statistics are found by a 4-level radix multi-select (12, 8, 8 and 3
+ * Order statistics are found by a 4-level radix multi-select (12, 7, 6 and 6
  * bits) on the FP32 bit patterns with exact integer partial sums; only the final
  * cross-exponent reduction is FP64.  Geometric means take one more pass that sums ln kappa
  * (exponent in FP64, mantissa by FP32 logf) between consecutive order

@@ -7,12 +7,14 @@
 // For an order statistic theta = x_(k): S(k) = sum_{x < theta} x + (k - #{x < theta}) theta.
 //
 // Order statistics: MSB radix multi-select on the FP32 bit patterns (values are
-// non-negative, so the bit order is the value order) over four levels of 12, 8, 8
-// and 3 bits (bits 30..19, 18..11, 10..3, 2..0).  Every histogram bin carries the
-// count (high 24 bits) and the sum of the bits below the bin's prefix (low 40
-// bits) in one 64-bit shared-memory atomic.  Values of one exponent E are integers
-// in units of 2^(max(E,1)-150), so every partial sum inside an exponent group is
-// exact integer arithmetic; only the sum across the 256 exponent groups is FP64.
+// non-negative, so the bit order is the value order) over four levels of 12, 7, 6
+// and 6 bits (bits 30..19, 18..12, 11..6, 5..0).  Every histogram bin carries the
+// count and the exact sum of the bits below the bin's prefix, the latter as two
+// 32-bit sums (of bits >> 10 and of bits & 1023): 32-bit shared-memory atomics are
+// native and keep their rate when many lanes hit one bin, while 64-bit ones are not.
+// Values of one exponent E are integers in units of 2^(max(E,1)-150), so every partial
+// sum inside an exponent group is exact integer arithmetic; only the sum across the 256
+// exponent groups is FP64.
 //
 // Passes over the interval: pass 1 (from HBM) builds the level-1 histogram; pass 2
 // (from L2) copies the values that fall into a target's level-1 bin into a
@@ -46,11 +48,11 @@ constexpr int kMaxTargets = kMaxSteps - 1;
 constexpr int kL1Shift = 19;                       // level 1: bits 30..19
 constexpr int kL1Bins = 1 << (31 - kL1Shift);      // 4096
 constexpr int kL1PerGroup = 1 << (23 - kL1Shift);  // level-1 bins per exponent: 16
-constexpr int kMinSlots = 8;                       // h2 doubles as the 4096-int prefix array
-constexpr int kCand = 8192;                        // candidate buffer (32-bit patterns)
+constexpr int kL2Bins = 128;                       // widest deeper level (7 bits)
+constexpr int kMinSlots = 4;
+constexpr int kCand = 6144;                        // candidate buffer (32-bit patterns); doubles as
+                                                   // the 4096-int prefix array before collection
 constexpr long long kMaxInterval = 1ll << 21;      // count < 2^24 and low-bit sums < 2^40 per bin
-constexpr unsigned long long kOne = 1ull << 40;
-constexpr unsigned long long kLowMask = kOne - 1;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Target {
@@ -128,55 +130,43 @@ __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long
     f(t0 + tid < n ? __float_as_uint(__ldg(x + t0 + tid)) : 0u, t0 + tid < n);
 }
 
-// Histogram add of one value per lane (count in the high 24 bits, low bits below the
-// bin's prefix in the low 40).  Called by all 32 lanes; key < 0 adds nothing.
-//   ODF_AGG 0: one atomic per lane;
-//   ODF_AGG 1: when every lane of the warp has the same key (smooth stretches of an
-//              opacity array), one atomic for the warp with the reduced low-bit sum
-//              (each low part < 2^19, so 32 of them fit 32 bits), else one per lane;
-//   ODF_AGG 2: lanes with equal keys aggregated by match + reduce, one atomic per key.
-#ifndef ODF_AGG
-#define ODF_AGG 1
-#endif
-__device__ __forceinline__ void agg_add(unsigned long long* __restrict__ h, int key, unsigned low, int lane) {
-#if ODF_AGG == 2
-    const unsigned peers = __match_any_sync(kFull, key);
-    const unsigned sum = __reduce_add_sync(peers, low);
-    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[key], ((unsigned long long)__popc(peers) << 40) + sum);
-#elif ODF_AGG == 1
-    const int kmin = __reduce_min_sync(kFull, key), kmax = __reduce_max_sync(kFull, key);
-    if (kmin == kmax) {
-        if (kmin >= 0) {
-            const unsigned sum = __reduce_add_sync(kFull, low);
-            if (lane == 0) atomicAdd(&h[kmin], (32ull << 40) + sum);
-        }
-    } else if (key >= 0) {
-        atomicAdd(&h[key], kOne + low);
+// A histogram of nb bins in shared memory: per bin the count and the sum of the values
+// low parts (each < 2^20), kept exactly as two 32-bit sums of (low >> 10) and (low & 1023):
+// an interval has fewer than 2^21 values, so neither sum can overflow.
+struct Hist {
+    unsigned* c;
+    unsigned* hi;
+    unsigned* lo;
+    __device__ __forceinline__ void add(int k, unsigned n, unsigned shi, unsigned slo) const {
+        atomicAdd(c + k, n);
+        if (shi) atomicAdd(hi + k, shi);
+        if (slo) atomicAdd(lo + k, slo);
     }
-#else
-    if (key >= 0) atomicAdd(&h[key], kOne + low);
-#endif
-}
+    __device__ __forceinline__ unsigned long long count(int k) const { return c[k]; }
+    __device__ __forceinline__ unsigned long long low(int k) const {
+        return ((unsigned long long)hi[k] << 10) + lo[k];
+    }
+    __device__ __forceinline__ void zero(int k) const { c[k] = 0u; hi[k] = 0u; lo[k] = 0u; }
+};
 
-// Per-thread run merging of histogram adds (CHUNKED passes): consecutive values of a
-// thread's chunk that fall into the same bin are summed in registers and one shared-memory
-// atomic is issued per run.
+// Per-thread run merging of histogram adds: consecutive values of a thread that fall
+// into the same bin are summed in registers and flushed with one set of atomics per run.
 struct RunAdd {
     int key = -1;
-    unsigned long long val = 0;
-    __device__ __forceinline__ void add(unsigned long long* __restrict__ h, int k, unsigned long long v) {
-        if (k == key) {
-            val += v;
-        } else {
-            if (key >= 0) atomicAdd(&h[key], val);
+    unsigned n = 0, shi = 0, slo = 0;
+    __device__ __forceinline__ void add(const Hist& h, int k, unsigned low) {
+        if (k != key) {
+            if (key >= 0) h.add(key, n, shi, slo);
             key = k;
-            val = v;
+            n = shi = slo = 0u;
         }
+        ++n;
+        shi += low >> 10;
+        slo += low & 1023u;
     }
-    __device__ __forceinline__ void flush(unsigned long long* __restrict__ h) {
-        if (key >= 0) atomicAdd(&h[key], val);
+    __device__ __forceinline__ void flush(const Hist& h) {
+        if (key >= 0) h.add(key, n, shi, slo);
         key = -1;
-        val = 0;
     }
 };
 
@@ -236,8 +226,7 @@ __device__ __forceinline__ double ln_f32_bits(unsigned bits) {
 // One warp resolves one target inside its slot's 2^wb-bin histogram h (packed counts and
 // low-bit sums): finds the sub-bin holding rank t.k and adds the counts and exact sums
 // of all lower sub-bins.
-__device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long* __restrict__ h, int wb, int sh,
-                                             int lane) {
+__device__ __forceinline__ void resolve_warp(Target& t, const Hist& h, int wb, int sh, int lane) {
     const int nb = 1 << wb;
     const int per = nb >= 32 ? nb / 32 : 1;
     const unsigned E = t.prefix >> 23;
@@ -245,7 +234,7 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
     long long cnt = 0;
     for (int m = 0; m < per; ++m) {
         const int b = lane * per + m;
-        if (b < nb) cnt += (long long)(h[b] >> 40);
+        if (b < nb) cnt += (long long)h.count(b);
     }
     long long incl = cnt;
     for (int d = 1; d < 32; d <<= 1) {
@@ -262,17 +251,17 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
     if (lane < ow) {
         for (int m = 0; m < per; ++m) {
             const int b = lane * per + m;
-            if (b < nb) ivs += (h[b] >> 40) * (pbase + ((unsigned long long)b << sh)) + (h[b] & kLowMask);
+            if (b < nb) ivs += h.count(b) * (pbase + ((unsigned long long)b << sh)) + h.low(b);
         }
     } else if (lane == ow) {
         long long run = before;
         for (int m = 0; m < per; ++m) {
             const int b = lane * per + m;
             if (b >= nb) break;
-            const long long c = (long long)(h[b] >> 40);
+            const long long c = (long long)h.count(b);
             if (t.k < run + c) { found = b; break; }
             run += c;
-            ivs += (unsigned long long)c * (pbase + ((unsigned long long)b << sh)) + (h[b] & kLowMask);
+            ivs += (unsigned long long)c * (pbase + ((unsigned long long)b << sh)) + h.low(b);
         }
         cnt_below = run;
     }
@@ -282,7 +271,7 @@ __device__ __forceinline__ void resolve_warp(Target& t, const unsigned long long
     if (lane == 0) {
         t.iv_lt += ivs;
         t.cnt_lt = cnt_below;
-        t.cnt_in = (long long)(h[found] >> 40);
+        t.cnt_in = (long long)h.count(found);
         t.prefix |= (unsigned)found << sh;
     }
 }
@@ -291,15 +280,17 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
                                                      const int64_t* __restrict__ bounds, int n_steps,
                                                      const double* __restrict__ cw, const double* __restrict__ w,
                                                      double* __restrict__ out, int geom) {
-    extern __shared__ unsigned long long sm[];
+    extern __shared__ __align__(16) unsigned sm[];
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
-    unsigned long long* h1 = sm;                             // [4096]
-    unsigned long long* h2 = sm + kL1Bins;                   // [nslots][256]; first 16 KB double as cincl
-    int* cincl = reinterpret_cast<int*>(h2);                 // [4096] inclusive prefix counts (before the levels)
-    unsigned* cand = reinterpret_cast<unsigned*>(h2 + (size_t)nslots * 256);   // [kCand]
+    const Hist h1{sm, sm + kL1Bins, sm + 2 * kL1Bins};                 // [4096] each
+    unsigned* h2base = sm + 3 * kL1Bins;
+    const int n2 = nslots * kL2Bins;
+    const Hist h2{h2base, h2base + n2, h2base + 2 * n2};               // [nslots][128] each
+    unsigned* cand = h2base + 3 * n2;                                  // [kCand]
+    int* cincl = reinterpret_cast<int*>(cand);               // [4096] inclusive prefix counts (before collection)
     short* slot1 = reinterpret_cast<short*>(cand + kCand);   // [4096]: level-1 bin -> slot
-    short* slot2 = slot1 + kL1Bins;                          // [nslots][256]: 20-bit prefix -> slot
+    short* slot2 = slot1 + kL1Bins;                          // [nslots][128]: 19-bit prefix -> slot
     __shared__ unsigned tbits[kL1Bins / 32];                 // bitmap of the targets' level-1 bins
     __shared__ unsigned long long gsum[256];
     __shared__ double gpre[257];
@@ -318,7 +309,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     const float* x = kappa + (size_t)row * N + b0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    for (int i = tid; i < kL1Bins; i += kOdfThreads) { h1[i] = 0ull; slot1[i] = -1; }
+    for (int i = tid; i < kL1Bins; i += kOdfThreads) { h1.zero(i); slot1[i] = -1; }
     if (tid < kL1Bins / 32) tbits[tid] = 0u;
     if (tid == 0) { s_zero = 0u; n_cand = 0; }
     __syncthreads();
@@ -331,7 +322,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
             if (!valid) return;
             bits &= 0x7fffffffu;
             zeros += bits == 0u ? 1u : 0u;
-            run.add(h1, (int)(bits >> kL1Shift), kOne | (unsigned long long)(bits & ((1u << kL1Shift) - 1u)));
+            run.add(h1, (int)(bits >> kL1Shift), bits & ((1u << kL1Shift) - 1u));
         });
         run.flush(h1);
         zeros = __reduce_add_sync(kFull, zeros);
@@ -342,7 +333,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     // ---- inclusive scan of the level-1 counts (8 bins per thread)
     {
         int c[8], v = 0;
-        for (int m = 0; m < 8; ++m) { c[m] = (int)(h1[8 * tid + m] >> 40); v += c[m]; }
+        for (int m = 0; m < 8; ++m) { c[m] = (int)h1.count(8 * tid + m); v += c[m]; }
         int incl = v;
         for (int d = 1; d < 32; d <<= 1) {
             int y = __shfl_up_sync(kFull, incl, d);
@@ -365,8 +356,8 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     if (tid < 256) {
         unsigned long long acc = 0;
         for (int m = 0; m < kL1PerGroup; ++m) {
-            const unsigned long long h = h1[tid * kL1PerGroup + m];
-            acc += (h >> 40) * (group_base(tid) + ((unsigned long long)m << kL1Shift)) + (h & kLowMask);
+            const int b = tid * kL1PerGroup + m;
+            acc += h1.count(b) * (group_base(tid) + ((unsigned long long)m << kL1Shift)) + h1.low(b);
         }
         gsum[tid] = acc;
     }
@@ -410,16 +401,15 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
                 else lo = mid + 1;
             }
             const int bb = lo;
-            const long long cnt = (long long)(h1[bb] >> 40);
+            const long long cnt = (long long)h1.count(bb);
             t.prefix = (unsigned)bb << kL1Shift;
             t.cnt_lt = (long long)cincl[bb] - cnt;
             t.cnt_in = cnt;
             unsigned long long acc = 0;
             const unsigned E = (unsigned)bb / kL1PerGroup;
             for (int m = bb & ~(kL1PerGroup - 1); m < bb; ++m) {
-                const unsigned long long h = h1[m];
-                acc += (h >> 40) * (group_base(E) + ((unsigned long long)(m & (kL1PerGroup - 1)) << kL1Shift)) +
-                       (h & kLowMask);
+                acc += h1.count(m) * (group_base(E) + ((unsigned long long)(m & (kL1PerGroup - 1)) << kL1Shift)) +
+                       h1.low(m);
             }
             t.iv_lt = acc;
         }
@@ -432,8 +422,8 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     // values and every remaining level runs on the buffer.  Until then each level is a
     // histogram pass over the interval (from L2) restricted to the target prefixes, found
     // with O(1) prefix -> slot tables (slot1 at 12 resolved bits, slot2 at 20).
-    const int shifts[3] = {11, 3, 0};
-    const int widths[3] = {8, 8, 3};
+    const int shifts[3] = {12, 6, 0};
+    const int widths[3] = {7, 6, 6};
     bool have_cand = false;
     int nc = 0;
     int nd_prev = 0;
@@ -471,22 +461,22 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
         if (lvl == 0) {
             for (int q = tid; q < nd; q += kOdfThreads) slot1[dpre[q] >> kL1Shift] = (short)q;
         } else if (lvl == 1) {
-            for (int i = tid; i < nd_prev * 256; i += kOdfThreads) slot2[i] = -1;
+            for (int i = tid; i < nd_prev * kL2Bins; i += kOdfThreads) slot2[i] = -1;
         }
         __syncthreads();
         if (lvl == 1)
             for (int q = tid; q < nd; q += kOdfThreads) {
                 const int q1 = slot1[dpre[q] >> kL1Shift];
-                if (q1 >= 0) slot2[q1 * 256 + ((dpre[q] >> 11) & 255u)] = (short)q;
+                if (q1 >= 0) slot2[q1 * kL2Bins + ((dpre[q] >> 12) & (kL2Bins - 1))] = (short)q;
             }
-        for (int i = tid; i < nd * 256; i += kOdfThreads) h2[i] = 0ull;
+        for (int i = tid; i < nd * kL2Bins; i += kOdfThreads) h2.zero(i);
         __syncthreads();
         // slot of a value at the current depth, or -1 (zeros are never in a slot)
         auto slot_of = [&](unsigned bits) -> int {
             if (bits == 0u) return -1;
             const int q1 = slot1[bits >> kL1Shift];
             if (q1 < 0 || lvl == 0) return q1;
-            if (lvl == 1) return slot2[q1 * 256 + ((bits >> 11) & 255u)];
+            if (lvl == 1) return slot2[q1 * kL2Bins + ((bits >> 12) & (kL2Bins - 1))];
             const unsigned pre = (bits >> hiShift) << hiShift;
             int q = -1;
             for (int r = 0; r < nd; ++r)
@@ -518,7 +508,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
                 const int q = i < nc ? slot_of(bits) : -1;
                 const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
                 const unsigned low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
-                agg_add(h2, q >= 0 ? q * 256 + (int)sub : -1, low, lane);
+                if (q >= 0) h2.add(q * kL2Bins + (int)sub, 1u, low >> 10, low & 1023u);
             }
         } else {
             RunAdd run;
@@ -527,18 +517,19 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
                 const int q = valid ? slot_of(bits) : -1;
                 if (q < 0) return;
                 const unsigned sub = (bits >> sh) & (unsigned)(nbins - 1);
-                const unsigned long long low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
-                run.add(h2, q * 256 + (int)sub, kOne | low);
+                const unsigned low = sh ? (bits & ((1u << sh) - 1u)) : 0u;
+                run.add(h2, q * kL2Bins + (int)sub, low);
             });
             run.flush(h2);
         }
         __syncthreads();
-        if (tid < nd && dpre[tid] == 0u) h2[tid * 256] += (unsigned long long)s_zero << 40;
+        if (tid < nd && dpre[tid] == 0u) h2.c[tid * kL2Bins] += s_zero;
         __syncthreads();
         for (int t = warp; t < nt; t += kOdfWarps) {
             if (tg[t].total) continue;
             Target tt = tg[t];
-            resolve_warp(tt, h2 + tt.slot * 256, wb, sh, lane);
+            const Hist hs{h2.c + tt.slot * kL2Bins, h2.hi + tt.slot * kL2Bins, h2.lo + tt.slot * kL2Bins};
+            resolve_warp(tt, hs, wb, sh, lane);
             if (lane == 0) tg[t] = tt;
         }
         nd_prev = nd;
@@ -620,8 +611,9 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
 size_t odf_smem_bytes(int n_steps) {
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
-    return (kL1Bins + (size_t)nslots * 256) * sizeof(unsigned long long) + kCand * sizeof(unsigned) +
-           (kL1Bins + (size_t)nslots * 256) * sizeof(short);
+    static_assert(kCand >= kL1Bins, "the candidate buffer holds the prefix counts");
+    return 3 * (kL1Bins + (size_t)nslots * kL2Bins) * sizeof(unsigned) + kCand * sizeof(unsigned) +
+           (kL1Bins + (size_t)nslots * kL2Bins) * sizeof(short);
 }
 
 }  // namespace

@@ -570,14 +570,20 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
     const int J0 = tile * TILE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    float jf[PTS], G[PTS], sum[PTS], comp[PTS], part[PTS];
+    // Kahan totals live in shared memory ([point][thread], conflict-free): they change once
+    // per chunk, and keeping them out of registers lets more CTAs share an SM
+    __shared__ float sSum[PREC == MPSA_PREC_FP32_COMPENSATED ? PTS : 1][THREADS];
+    __shared__ float sComp[PREC == MPSA_PREC_FP32_COMPENSATED ? PTS : 1][THREADS];
+    float jf[PTS], G[PTS], part[PTS];
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
         const int off = k * THREADS + tid;
         jf[k] = (float)(J0 + off);
         G[k] = expm1f(-(float)off * g.lnq);
-        sum[k] = 0.f;
-        comp[k] = 0.f;
+        if (PREC == MPSA_PREC_FP32_COMPENSATED) {
+            sSum[k][tid] = 0.f;
+            sComp[k][tid] = 0.f;
+        }
         part[k] = 0.f;
     }
 
@@ -741,10 +747,11 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                 // fold the chunk's FP32 partial sums into the Kahan-compensated totals
 #pragma unroll
                 for (int k = 0; k < PTS; ++k) {
-                    const float y = part[k] - comp[k];
-                    const float t = sum[k] + y;
-                    comp[k] = (t - sum[k]) - y;
-                    sum[k] = t;
+                    const float s0 = sSum[k][tid], c0 = sComp[k][tid];
+                    const float y = part[k] - c0;
+                    const float t = s0 + y;
+                    sComp[k][tid] = (t - s0) - y;
+                    sSum[k][tid] = t;
                     part[k] = 0.f;
                 }
             }
@@ -755,7 +762,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
 #pragma unroll
     for (int k = 0; k < PTS; ++k) {
         const int j = J0 + k * THREADS + tid;
-        const float tot = (PREC == MPSA_PREC_FP32_COMPENSATED) ? (sum[k] - comp[k]) : part[k];
+        const float tot = (PREC == MPSA_PREC_FP32_COMPENSATED) ? (sSum[k][tid] - sComp[k][tid]) : part[k];
         if (j < g.N) g.out[j] = tp * tot;
     }
 }
@@ -807,7 +814,7 @@ __device__ __forceinline__ RowDesc row_desc(const TileArgs& g, int s, int tile) 
 }
 
 #ifndef MPSA_TILES_MINB
-#define MPSA_TILES_MINB 3
+#define MPSA_TILES_MINB 4
 #endif
 template <int PREC>
 __global__ void __launch_bounds__(kTileThreads, MPSA_TILES_MINB) k_tiles(TileArgs g) {
@@ -1160,7 +1167,7 @@ namespace {
 struct TuneCfg {
     int pts, threads, minb;
 };
-constexpr TuneCfg kCfgs[] = {{8, 256, 3}, {4, 256, 4}, {8, 128, 6}, {16, 128, 2}};
+constexpr TuneCfg kCfgs[] = {{8, 256, 4}, {4, 256, 4}, {8, 128, 8}, {16, 128, 3}};
 constexpr int kNumCfgs = sizeof(kCfgs) / sizeof(kCfgs[0]);
 
 template <int PREC, int PTS, int THREADS, int MINB>
@@ -1181,17 +1188,17 @@ int persistent_launch(int cfg, int prec, const RowDesc* rows, const int2* units,
     MPSA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     if (prec == MPSA_PREC_FP32_NAIVE) {
         switch (cfg) {
-            case 0: return persistent_launch_t<1, 8, 256, 3>(rows, units, n_units, counter, st);
+            case 0: return persistent_launch_t<1, 8, 256, 4>(rows, units, n_units, counter, st);
             case 1: return persistent_launch_t<1, 4, 256, 4>(rows, units, n_units, counter, st);
-            case 2: return persistent_launch_t<1, 8, 128, 6>(rows, units, n_units, counter, st);
-            default: return persistent_launch_t<1, 16, 128, 2>(rows, units, n_units, counter, st);
+            case 2: return persistent_launch_t<1, 8, 128, 8>(rows, units, n_units, counter, st);
+            default: return persistent_launch_t<1, 16, 128, 3>(rows, units, n_units, counter, st);
         }
     }
     switch (cfg) {
-        case 0: return persistent_launch_t<0, 8, 256, 3>(rows, units, n_units, counter, st);
+        case 0: return persistent_launch_t<0, 8, 256, 4>(rows, units, n_units, counter, st);
         case 1: return persistent_launch_t<0, 4, 256, 4>(rows, units, n_units, counter, st);
-        case 2: return persistent_launch_t<0, 8, 128, 6>(rows, units, n_units, counter, st);
-        default: return persistent_launch_t<0, 16, 128, 2>(rows, units, n_units, counter, st);
+        case 2: return persistent_launch_t<0, 8, 128, 8>(rows, units, n_units, counter, st);
+        default: return persistent_launch_t<0, 16, 128, 3>(rows, units, n_units, counter, st);
     }
 }
 
