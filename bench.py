@@ -337,13 +337,7 @@ def native_arm(args):
     evals_per_launch = evals_rank / max(tiles_n, 1)
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
     achieved = evals_per_launch * FLOP_PER_EVAL / (tiles_avg / 1e3) / 1e12
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof_path):
-        try:
-            traffic = json.load(open(prof_path)).get("k_tiles_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = measured_traffic("k_tiles", ["synth.cu", "voigt.cuh", "common.cuh"], sel)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_tiles (profile synthesis)",
                 "peak_kind": f"FP32 FMA peak {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
@@ -351,7 +345,8 @@ def native_arm(args):
     odf_avg = odf_ms / max(odf_n, 1)
     odf_bytes = B * N * 4 + B * K * 12 * 8
     roofline_odf = {"bound": "hbm", "achieved": odf_bytes / (odf_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": odf_bytes / (odf_avg / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_odf (build_odf)",
+                    "frac": odf_bytes / (odf_avg / 1e3) / 1e9 / hbm,
+                    "traffic": measured_traffic("k_odf", ["odf.cu", "common.cuh"], sel), "kernel": "k_odf (build_odf)",
                     "peak_kind": f"{peak_kind} HBM copy bandwidth", "avg_launch_ms": odf_avg, "launches": odf_n}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -618,6 +613,30 @@ def precision_arm(args):
         out["variants"][names[prec]] = {"opacity_max_rel": float(rel.max()), "opacity_p99_rel": float(np.quantile(rel, 0.99)),
                                         "odf_max_rel": float(ro.max()), "odf_p99_rel": float(np.quantile(ro, 0.99))}
     print(json.dumps(out), flush=True)
+
+
+def measured_traffic(kernel, sources, rows):
+    """DRAM bytes (read + written) per launch of `kernel` from the ncu summary in
+    profiles/traffic_table_workload.md, or None when that capture was taken on other rows
+    or on kernel sources that have changed since (recorded as SHA-1 of the files)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "traffic_table_workload.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = hashlib.sha1()
+    for f in sources:
+        with open(os.path.join(ROOT, "paper_2105_13611_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    m_rows = re.search(r"^rows: ([0-9,]+)$", text, re.M)
+    m_src = re.search(rf"^{kernel}_source_sha1: ([0-9a-f]+)$", text, re.M)
+    m_val = re.search(rf"^{kernel}_bytes_per_launch: ([0-9]+)$", text, re.M)
+    if not (m_rows and m_src and m_val):
+        return None
+    if [int(r) for r in m_rows.group(1).split(",")] != [int(r) for r in rows] or m_src.group(1) != h.hexdigest():
+        return None
+    return int(m_val.group(1))
 
 
 def main():

@@ -37,7 +37,11 @@ namespace {
 constexpr float kLn10 = 2.302585092994046f;
 constexpr float kFourPi = 12.566370614359172f;
 constexpr float kFarV = 41.f;            // far formula valid for |v| >= 40
-constexpr int kFarDist = 8 * kTile;      // far formula precise when the centre is this far away
+// The far evaluation v = G_k (kv B) + kv E1 rounds two terms, each at most the larger of
+// the tile's span and the centre's distance in x = d ln q; with the centre at least one
+// tile (2048 points) from every point of the tile, |x| is at least that span, so v keeps
+// about 2e-7 relative accuracy.
+constexpr int kFarDist = kTile;
 
 __device__ __forceinline__ int floordiv(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
@@ -248,6 +252,17 @@ __device__ __forceinline__ float d_blue(float vv, float kv, float lnq) { return 
 
 constexpr unsigned char kDropped = 255;
 
+// The tile kernel's constants of one kept (row, line), stored in bucket order so that a
+// tile's candidates are one contiguous run of records (three 16-byte loads per line)
+// instead of gathers from nine line-indexed arrays.
+struct __align__(16) LineRec {
+    int c;
+    float f, kv, a;
+    float srel;
+    int jlo, jhi, ilo;
+    int ihi, pad0, pad1, pad2;
+};
+
 struct PrepOut {
     int* c;
     float* f;
@@ -393,7 +408,7 @@ __global__ void k_scan(int nb, int* __restrict__ blkcnt, int* __restrict__ class
 __global__ void __launch_bounds__(256) k_scatter(int64_t L, int N, const unsigned char* __restrict__ cls,
                                                  const int* __restrict__ cpos, const int* __restrict__ blkoff,
                                                  const int* __restrict__ classbase, int nb, int* __restrict__ bidx,
-                                                 int* __restrict__ bkey) {
+                                                 int* __restrict__ bkey, const PrepOut o, LineRec* __restrict__ rec) {
     __shared__ int wcnt[8][kNumClasses];
     const int s = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,6 +429,19 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t L, int N, const unsigne
         const int c = cpos[i];
         bidx[(size_t)s * L + pos] = (int)i;
         bkey[(size_t)s * L + pos] = c < -1 ? -1 : (c > N ? N : c);
+        const size_t q = (size_t)s * L + i;
+        LineRec r;
+        r.c = o.c[q];
+        r.f = o.f[q];
+        r.kv = o.kv[q];
+        r.a = o.a[q];
+        r.srel = o.srel[q];
+        r.jlo = o.jlo[q];
+        r.jhi = o.jhi[q];
+        r.ilo = o.ilo[q];
+        r.ihi = o.ihi[q];
+        r.pad0 = r.pad1 = r.pad2 = 0;
+        rec[(size_t)s * L + pos] = r;
     }
 }
 
@@ -447,6 +475,7 @@ struct RowDesc {
     const float* ln_tp;         // ln of the cut threshold t_p (outputs are t_p * sum of s_rel H)
     const int* cum;             // [kNumClasses][nT + 3]
     const int* bidx;            // [L] bucketed line indices
+    const LineRec* rec;         // [L] their constants, in the same order
     const int* c;
     const float* f;
     const float* srel;
@@ -602,14 +631,16 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
             float4 fa, fb;
             NearRec nr;
             if (pos < end) {
-                const int q = g.bidx[pos];
-                const int jlo = g.jlo[q], jhi = g.jhi[q];
+                const int4* rp = reinterpret_cast<const int4*>(g.rec + pos);
+                const int4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2);
+                const int jlo = r1.y, jhi = r1.z;
                 if (jhi >= J0 && jlo <= J0 + TILE - 1) {
-                    const int c = g.c[q];
-                    const float f = g.f[q], kv = g.kv[q], a = g.a[q], srel = g.srel[q];
+                    const int c = r0.x;
+                    const float f = __int_as_float(r0.y), kv = __int_as_float(r0.z), a = __int_as_float(r0.w),
+                                srel = __int_as_float(r1.x);
                     const int klo = max(0, (jlo - J0) / THREADS), khi = min(PTS - 1, (jhi - J0) / THREADS);
                     const int P0 = J0 + klo * THREADS, P1 = J0 + khi * THREADS + THREADS - 1;
-                    const bool check = !(g.ilo[q] <= P0 && g.ihi[q] >= P1);
+                    const bool check = !(r1.w <= P0 && r2.x >= P1);
                     // distance from the centre x0 = c + f to the nearest point of the tile
                     // (far lines are evaluated at all points, masked to [klo, khi])
                     const int T0 = J0, T1 = J0 + TILE - 1;
@@ -774,6 +805,7 @@ struct TileArgs {
     float lnq, q1, q2, q3;
     const int* cum;
     const int* bidx;
+    const LineRec* rec;
     const int* c;
     const float* f;
     const float* srel;
@@ -800,6 +832,7 @@ __device__ __forceinline__ RowDesc row_desc(const TileArgs& g, int s, int tile) 
     r.ln_tp = g.ln_tp + s;
     r.cum = g.cum + (size_t)s * kNumClasses * (g.nT + 3);
     r.bidx = g.bidx + sL;
+    r.rec = g.rec + sL;
     r.c = g.c + sL;
     r.f = g.f + sL;
     r.srel = g.srel + sL;
@@ -973,6 +1006,7 @@ struct PrepBufs {
     double lnq = 0.0;
     int *c = nullptr, *bidx = nullptr, *bkey = nullptr, *blkcnt = nullptr, *classbase = nullptr, *classcnt = nullptr,
         *cum = nullptr;
+    LineRec* rec = nullptr;
     float *f = nullptr, *lamcm = nullptr, *lnS = nullptr, *av = nullptr, *lnk0 = nullptr, *ln_tp = nullptr;
     RowConst* rc = nullptr;
     SpConst* spc = nullptr;
@@ -1000,7 +1034,8 @@ int prep_alloc(PrepBufs& b, const mpsa_ctx* ctx, int n_sel, int N, double R, int
         (r = al(&b.po.jhi, SL)) || (r = al(&b.po.ilo, SL)) || (r = al(&b.po.ihi, SL)) || (r = al(&b.po.cls, SL)) ||
         (r = al(&b.blkcnt, (size_t)n_sel * kNumClasses * b.nb)) || (r = al(&b.wpart, (size_t)n_sel * b.nb)) ||
         (r = al(&b.classbase, (size_t)n_sel * kNumClasses)) || (r = al(&b.classcnt, (size_t)n_sel * kNumClasses)) ||
-        (r = al(&b.bidx, SL)) || (r = al(&b.bkey, SL)) || (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))))
+        (r = al(&b.bidx, SL)) || (r = al(&b.bkey, SL)) || (r = al(&b.rec, SL)) ||
+        (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))))
         return r;
     b.po.blkcnt = b.blkcnt;
     b.po.wpart = b.wpart;
@@ -1028,7 +1063,8 @@ int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const
     k_prep<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc, b.lnS, b.av,
                                               b.lnk0, b.ln_tp, b.nb, b.po);
     k_scan<<<n_sel, 32 * 8, 0, st>>>(b.nb, b.blkcnt, b.classbase, b.classcnt, b.wpart, (long long*)evals);
-    k_scatter<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx, b.bkey);
+    k_scatter<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx, b.bkey,
+                                                 b.po, b.rec);
     return ranges_launch(b, b.tile, b.cum, st);
 }
 
@@ -1052,6 +1088,7 @@ TileArgs tile_args(const PrepBufs& b, float* kappa) {
     ta.q3 = (float)(-b.lnq * b.lnq * b.lnq / 24.0);
     ta.cum = b.cum;
     ta.bidx = b.bidx;
+    ta.rec = b.rec;
     ta.c = b.po.c;
     ta.f = b.po.f;
     ta.srel = b.po.srel;
@@ -1291,6 +1328,7 @@ std::vector<RowDesc> row_descs(mpsa_batch* b, int tile, const std::vector<int*>&
             r.ln_tp = G.pb.ln_tp + s;
             r.cum = cums[g] + (size_t)s * kNumClasses * (nT + 3);
             r.bidx = G.pb.bidx + sL;
+            r.rec = G.pb.rec + sL;
             r.c = G.pb.po.c + sL;
             r.f = G.pb.po.f + sL;
             r.srel = G.pb.po.srel + sL;
