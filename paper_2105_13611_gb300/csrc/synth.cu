@@ -495,6 +495,7 @@ constexpr int kFlChk = 1 << 10;      // points near the cut: test s_rel H >= 1
 constexpr int kFlAlt = 1 << 11;      // far: "y" form; near: expm1 series for v
 constexpr int kFlFull = 1 << 12;     // the window covers every slot of the tile
 constexpr int kFlRat = 1 << 13;      // far: rational form sk / (|z|^2 - 3/2)
+constexpr int kFlSmall = 1 << 14;    // far, rational: |v| < 1e6 on the tile (three points per reciprocal)
 
 struct NearRec {
     float cf, f, klnq, a, srel, kv;
@@ -521,20 +522,43 @@ struct NearRec {
 //    r = 1/(D_0 D_1), sk/D_0 = (sk r) D_1 and sk/D_1 = (sk r) D_0 (relative error about
 //    two ulps); per evaluation 4 FP32 instructions and half a reciprocal.  Used where
 //    |v| < 1e9 on the whole tile, so that D_0 D_1 < 1e36 stays finite.
-constexpr int kFarRat = 0, kFarExact = 1, kFarY = 2, kFarRatPair = 3;
+//  * kFarRatTriple: one reciprocal for three points, r = 1/(D_0 D_1 D_2), with
+//    sk/D_0 = (sk r D_2) D_1, sk/D_1 = (sk r D_2) D_0 and sk/D_2 = (sk r) (D_0 D_1) (about
+//    four ulps); per evaluation 4.67 FP32 instructions and a third of a reciprocal, for
+//    lines with |v| < 1e6 on the tile (D_0 D_1 D_2 < 1e36).  The remaining points of a
+//    thread (PTS not a multiple of three) use the paired or single form.
+constexpr int kFarRat = 0, kFarExact = 1, kFarY = 2, kFarRatPair = 3, kFarRatTriple = 4;
 
 template <int PTS, int FORM, bool MASKED>
 __device__ __forceinline__ void far_line(const float4 p, const float2 q, int klo, int khi, bool chk,
                                          const float (&G)[PTS], float (&part)[PTS]) {
-    if constexpr (FORM == kFarRatPair) {
-        static_assert(PTS % 2 == 0 && !MASKED, "paired form: plain lines, even point count");
+    if constexpr (FORM == kFarRatPair || FORM == kFarRatTriple) {
+        static_assert(!MASKED, "grouped forms: plain lines only");
+        constexpr int T3 = FORM == kFarRatTriple ? PTS / 3 : 0;   // triples, then pairs, then a single
 #pragma unroll
-        for (int k = 0; k < PTS; k += 2) {
+        for (int t = 0; t < T3; ++t) {
+            const int k = 3 * t;
+            const float v0 = fmaf(G[k], p.x, p.y), v1 = fmaf(G[k + 1], p.x, p.y), v2 = fmaf(G[k + 2], p.x, p.y);
+            const float D0 = fmaf(v0, v0, p.z), D1 = fmaf(v1, v1, p.z), D2 = fmaf(v2, v2, p.z);
+            const float P01 = D0 * D1;
+            const float sr = p.w * rcp_approx(P01 * D2);
+            const float s2 = sr * D2;
+            part[k] = fmaf(s2, D1, part[k]);
+            part[k + 1] = fmaf(s2, D0, part[k + 1]);
+            part[k + 2] = fmaf(sr, P01, part[k + 2]);
+        }
+#pragma unroll
+        for (int k = 3 * T3; k + 1 < PTS; k += 2) {
             const float v0 = fmaf(G[k], p.x, p.y), v1 = fmaf(G[k + 1], p.x, p.y);
             const float D0 = fmaf(v0, v0, p.z), D1 = fmaf(v1, v1, p.z);
             const float sr = p.w * rcp_approx(D0 * D1);
             part[k] = fmaf(sr, D1, part[k]);
             part[k + 1] = fmaf(sr, D0, part[k + 1]);
+        }
+        if constexpr ((PTS - 3 * T3) % 2 == 1) {
+            const int k = PTS - 1;
+            const float v0 = fmaf(G[k], p.x, p.y);
+            part[k] = fmaf(p.w, rcp_approx(fmaf(v0, v0, p.z)), part[k]);
         }
     } else {
 #pragma unroll
@@ -594,7 +618,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
     __shared__ float4 sFarA[THREADS];
     __shared__ float4 sFarB[THREADS];
     __shared__ NearRec sNear[THREADS];
-    __shared__ int sCnt[5][THREADS / 32];
+    __shared__ int sCnt[6][THREADS / 32];
 
     const int J0 = tile * TILE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -670,7 +694,10 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                         const float zmin2 = fmaf(vmin, vmin, A);
                         if (zmin2 * zmin2 >= 1.0e6f * fmaf(2.f, A, 2.f)) {
                             fa = make_float4(kv * B, kv * E1, A - 1.5f, sk);
-                            fb = make_float4(0.f, 0.f, __int_as_float(flags | kFlRat | (yform ? kFlAlt : 0)), 0.f);
+                            fb = make_float4(0.f, 0.f,
+                                             __int_as_float(flags | kFlRat | (yform ? kFlAlt : 0) |
+                                                            (vmax < 1.0e6f ? kFlSmall : 0)),
+                                             0.f);
                         } else {
                             fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
                             fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
@@ -692,64 +719,85 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                     }
                 }
             }
-            // far lines are compacted into four lists: plain rational, plain "exact" and plain
-            // "y" forms, and masked (partial coverage or cut test), so the hot loops dispatch
-            // nothing; near lines into a fifth
+            // far lines are compacted into five lists: plain rational with three or two points
+            // per reciprocal, plain "exact" and plain "y" forms, and masked (partial coverage or
+            // cut test), so the hot loops dispatch nothing; near lines into a sixth
+            constexpr int kNearCat = 5;
             int cat = -1;
             if (isFar) {
                 const int fl = __float_as_int(fb.z);
                 const bool plain = (fl & kFlFull) && !(fl & kFlChk);
                 // rational lines with |v| >= 1e9 somewhere take the single-reciprocal masked path
-                cat = plain ? ((fl & kFlRat) ? ((fl & kFlAlt) ? 3 : 0) : ((fl & kFlAlt) ? 2 : 1)) : 3;
+                cat = !plain ? 4
+                             : ((fl & kFlRat) ? ((fl & kFlAlt) ? 4 : ((fl & kFlSmall) ? 0 : 1)) : ((fl & kFlAlt) ? 3 : 2));
             } else if (isNear) {
-                cat = 4;
+                cat = kNearCat;
             }
             unsigned bm = 0u;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
+            for (int q = 0; q <= kNearCat; ++q) {
                 const unsigned b = __ballot_sync(0xffffffffu, cat == q);
                 if (cat == q) bm = b;
                 if (lane == 0) sCnt[q][warp] = __popc(b);
             }
             __syncthreads();
-            int off = 0, tot[5] = {0, 0, 0, 0, 0};
+            int off = 0, tot[kNearCat + 1] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int w = 0; w < THREADS / 32; ++w) {
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
+                for (int q = 0; q <= kNearCat; ++q) {
                     const int cnt = sCnt[q][w];
                     if (w < warp && q == cat) off += cnt;
                     tot[q] += cnt;
                 }
             }
             const unsigned lt = (1u << lane) - 1u;
-            if (cat >= 0 && cat < 4) {
+            if (cat >= 0 && cat < kNearCat) {
                 int base2 = 0;
 #pragma unroll
-                for (int q = 0; q < 3; ++q)
+                for (int q = 0; q < kNearCat - 1; ++q)
                     if (q < cat) base2 += tot[q];
                 const int p = base2 + off + __popc(bm & lt);
                 sFarA[p] = fa;
                 sFarB[p] = fb;
             }
-            if (cat == 4) sNear[off + __popc(bm & lt)] = nr;
-            const int nNear = tot[4];
+            if (cat == kNearCat) sNear[off + __popc(bm & lt)] = nr;
+            const int nNear = tot[kNearCat];
             __syncthreads();
 
             // ---- evaluation: every thread, every compacted line, its PTS points
             {
                 int r = 0;
-                for (; r < tot[0]; ++r)
+                // two lines per iteration: half the loop overhead, and two independent
+                // dependency chains per point for the scheduler
+                for (; r + 1 < tot[0]; r += 2) {
+                    const float4 pa = sFarA[r], pb = sFarA[r + 1];
+                    far_line<PTS, kFarRatTriple, false>(pa, make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                    far_line<PTS, kFarRatTriple, false>(pb, make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                }
+                if (r < tot[0]) {
+                    far_line<PTS, kFarRatTriple, false>(sFarA[r], make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                    ++r;
+                }
+                const int e1 = tot[0] + tot[1];
+                for (; r + 1 < e1; r += 2) {
+                    const float4 pa = sFarA[r], pb = sFarA[r + 1];
+                    far_line<PTS, kFarRatPair, false>(pa, make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                    far_line<PTS, kFarRatPair, false>(pb, make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
+                }
+                if (r < e1) {
                     far_line<PTS, kFarRatPair, false>(sFarA[r], make_float2(0.f, 0.f), 0, PTS - 1, false, G, part);
-                for (; r < tot[0] + tot[1]; ++r) {
+                    ++r;
+                }
+                for (; r < e1 + tot[2]; ++r) {
                     const float4 q4 = sFarB[r];
                     far_line<PTS, kFarExact, false>(sFarA[r], make_float2(q4.x, q4.y), 0, PTS - 1, false, G, part);
                 }
-                for (; r < tot[0] + tot[1] + tot[2]; ++r) {
+                for (; r < e1 + tot[2] + tot[3]; ++r) {
                     const float4 q4 = sFarB[r];
                     far_line<PTS, kFarY, false>(sFarA[r], make_float2(q4.x, q4.y), 0, PTS - 1, false, G, part);
                 }
-                for (; r < tot[0] + tot[1] + tot[2] + tot[3]; ++r) {
+                for (; r < e1 + tot[2] + tot[3] + tot[4]; ++r) {
                     const float4 p = sFarA[r];
                     const float4 q4 = sFarB[r];
                     const float2 q = make_float2(q4.x, q4.y);
