@@ -79,9 +79,14 @@ __global__ void k_populations(int rows, int n_points, int n_el, const double* __
         frac[e] = pow(10.0, leps[e] - 12.0) * abund[(size_t)comp * n_el + e] / eps_sum;
         phi[e] = 2.0 * U2[e] / U1[e] * saha * exp(-chi[e] * kEV / kT);
     }
+    // bisection in ln n_e down to adjacent doubles: stop when the midpoint no longer lies
+    // strictly between the bounds (a fixed width such as 1e-15 is below one ulp of ln n_e
+    // for |ln n_e| > 4 and would never be reached)
     double lo = log(1e-300), hi = log(n_tot);
-    for (int it = 0; it < 2000 && hi - lo > 1e-15; ++it) {
-        const double mid = 0.5 * (lo + hi), ne = exp(mid), nn = n_tot - ne;
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const double ne = exp(mid), nn = n_tot - ne;
         double ion = 0.0;
         for (int e = 0; e < n_el; ++e) ion += frac[e] * nn * phi[e] / (ne + phi[e]);
         if (ne - ion > 0.0) hi = mid; else lo = mid;

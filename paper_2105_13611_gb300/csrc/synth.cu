@@ -342,15 +342,18 @@ __global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const
                 atomicAdd(&cnt[cls], 1);
             }
         }
-        o.c[q] = c;
-        o.f[q] = f;
-        o.srel[q] = srel;
-        o.a[q] = a;
-        o.kv[q] = kv;
-        o.jlo[q] = jlo;
-        o.jhi[q] = jhi;
-        o.ilo[q] = ilo;
-        o.ihi[q] = ihi;
+        // only kept lines are read later (through their bucket), so dropped ones write the class alone
+        if (cls != kDropped) {
+            o.c[q] = c;
+            o.f[q] = f;
+            o.srel[q] = srel;
+            o.a[q] = a;
+            o.kv[q] = kv;
+            o.jlo[q] = jlo;
+            o.jhi[q] = jhi;
+            o.ilo[q] = ilo;
+            o.ihi[q] = ihi;
+        }
         o.cls[q] = cls;
     }
     // block sum of window lengths
