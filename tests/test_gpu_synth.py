@@ -75,6 +75,22 @@ def test_extreme_damping_and_pressures():
         assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
 
 
+def test_wide_grid_far_wing_forms():
+    # 9-10000 nm at R = 4000 (28k points, 14 tiles) with strongly damped rows: far wings span
+    # factors of tens in wavelength, so |v| passes 1e6 on many tiles (the paired-reciprocal
+    # far form) as well as staying below it (the three-point form)
+    w = wl.config_tiny(n_lines=80, lam=(9.0, 10000.0), R=4000.0, seed=21)
+    w.T = np.array([3000.0, 6000.0, 12000.0, 40000.0])
+    w.P = np.array([1e8, 1e7, 1e8, 1e6])
+    ctx, L = gpu_context(w)
+    kg, kcg, _ = gpu_synth(ctx, w, np.arange(4))
+    for s in range(4):
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        assert abs(kcg[s] / pl.kappa_c - 1) < 2e-5
+        bad, err, bound = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
+
+
 def test_full_size_sampled():
     # the 20,000-line, 575,365-point, 4-point workload in the launch configuration of the benchmark;
     # the oracle evaluates sampled grid points one by one (random points and the cores of strong lines)
