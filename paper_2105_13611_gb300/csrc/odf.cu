@@ -50,8 +50,10 @@ constexpr int kL1Bins = 1 << (31 - kL1Shift);      // 4096
 constexpr int kL1PerGroup = 1 << (23 - kL1Shift);  // level-1 bins per exponent: 16
 constexpr int kL2Bins = 128;                       // widest deeper level (7 bits)
 constexpr int kMinSlots = 4;
-constexpr int kCand = 6144;                        // candidate buffer (32-bit patterns); doubles as
-                                                   // the 4096-int prefix array before collection
+#ifndef ODF_KCAND
+#define ODF_KCAND 6144
+#endif
+constexpr int kCand = ODF_KCAND;                   // candidate buffer (32-bit patterns)
 constexpr long long kMaxInterval = 1ll << 21;      // count < 2^24 and low-bit sums < 2^40 per bin
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -284,21 +286,28 @@ __device__ __forceinline__ void resolve_warp(Target& t, const Hist& h, int wb, i
     }
 }
 
-__global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ kappa, int64_t N, int K,
+// CTAs per SM the kernel is compiled for (register budget: 3 x 512 threads x 40 registers).
+#ifndef ODF_MINB
+#define ODF_MINB 3
+#endif
+__global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __restrict__ kappa, int64_t N, int K,
                                                      const int64_t* __restrict__ bounds, int n_steps,
                                                      const double* __restrict__ cw, const double* __restrict__ w,
                                                      double* __restrict__ out, int geom) {
     extern __shared__ __align__(16) unsigned sm[];
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
+    // Two phases share the dynamic shared memory: until the targets are located it holds the
+    // level-1 histogram and its prefix counts; from then on (both dead) the candidates, the
+    // deeper histograms and the slot tables.  64 KB for 12 steps: three CTAs per SM.
     const Hist h1{sm, sm + kL1Bins, sm + 2 * kL1Bins};                 // [4096] each
-    unsigned* h2base = sm + 3 * kL1Bins;
+    int* cincl = reinterpret_cast<int*>(sm + 3 * kL1Bins);             // [4096] inclusive prefix counts
     const int n2 = nslots * kL2Bins;
+    unsigned* cand = sm;                                               // [kCand]
+    unsigned* h2base = sm + kCand;
     const Hist h2{h2base, h2base + n2, h2base + 2 * n2};               // [nslots][128] each
-    unsigned* cand = h2base + 3 * n2;                                  // [kCand]
-    int* cincl = reinterpret_cast<int*>(cand);               // [4096] inclusive prefix counts (before collection)
-    short* slot1 = reinterpret_cast<short*>(cand + kCand);   // [4096]: level-1 bin -> slot
-    short* slot2 = slot1 + kL1Bins;                          // [nslots][128]: 19-bit prefix -> slot
+    short* slot1 = reinterpret_cast<short*>(h2base + 3 * n2);          // [4096]: level-1 bin -> slot
+    short* slot2 = slot1 + kL1Bins;                                    // [nslots][128]: 19-bit prefix -> slot
     __shared__ unsigned tbits[kL1Bins / 32];                 // bitmap of the targets' level-1 bins
     __shared__ unsigned long long gsum[256];
     __shared__ double gpre[257];
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     const float* x = kappa + (size_t)row * N + b0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    for (int i = tid; i < kL1Bins; i += kOdfThreads) { h1.zero(i); slot1[i] = -1; }
+    for (int i = tid; i < kL1Bins; i += kOdfThreads) h1.zero(i);
     if (tid < kL1Bins / 32) tbits[tid] = 0u;
     if (tid == 0) { s_zero = 0u; n_cand = 0; }
     __syncthreads();
@@ -431,6 +440,9 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
     // values and every remaining level runs on the buffer.  Until then each level is a
     // histogram pass over the interval (from L2) restricted to the target prefixes, found
     // with O(1) prefix -> slot tables (slot1 at 12 resolved bits, slot2 at 20).
+    // the level phase starts: h1 and cincl are dead, their memory now holds the level data
+    for (int i = tid; i < kL1Bins; i += kOdfThreads) slot1[i] = -1;
+    __syncthreads();
     const int shifts[3] = {12, 6, 0};
     const int widths[3] = {7, 6, 6};
     bool have_cand = false;
@@ -647,9 +659,10 @@ __global__ void __launch_bounds__(kOdfThreads) k_odf(const float* __restrict__ k
 size_t odf_smem_bytes(int n_steps) {
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
-    static_assert(kCand >= kL1Bins, "the candidate buffer holds the prefix counts");
-    return 3 * (kL1Bins + (size_t)nslots * kL2Bins) * sizeof(unsigned) + kCand * sizeof(unsigned) +
-           (kL1Bins + (size_t)nslots * kL2Bins) * sizeof(short);
+    const size_t setup = 4 * (size_t)kL1Bins * sizeof(unsigned);
+    const size_t levels = (kCand + 3 * (size_t)nslots * kL2Bins) * sizeof(unsigned) +
+                          (kL1Bins + (size_t)nslots * kL2Bins) * sizeof(short);
+    return setup > levels ? setup : levels;
 }
 
 }  // namespace
