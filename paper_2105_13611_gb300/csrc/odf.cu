@@ -194,6 +194,67 @@ __device__ __forceinline__ void agg_append(unsigned* __restrict__ cand, int* n_c
     }
 }
 
+// Append every value x (bits with the sign cleared) of x[0..n) with take(x) to the candidate
+// buffer.  Warp-coalesced like for_each_value; each lane marks the takes among its 16 loaded
+// values, a warp scan gives every lane its offset, and one lane reserves the warp's total
+// with a single atomic per 512 values (instead of one atomic round trip per warp and value).
+template <class P>
+__device__ __forceinline__ void collect_values(const float* __restrict__ x, long long n, unsigned* __restrict__ cand,
+                                               int* n_cand, P&& take) {
+    constexpr int U = 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned mis = (unsigned)(((uintptr_t)x >> 2) & 3u);
+    long long head = mis ? (long long)(4u - mis) : 0;
+    if (head > n) head = n;
+    const float4* body = reinterpret_cast<const float4*>(x + head);
+    const long long nv = (n - head) >> 2;
+    const long long per = (((nv + kOdfWarps - 1) / kOdfWarps) + 31) & ~31ll;   // float4 per warp
+    const long long w0 = (long long)warp * per, w1 = min(w0 + per, nv);
+    for (long long it = w0; it < w0 + per; it += 32 * U) {
+        unsigned b[4 * U];
+        unsigned m = 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long i = it + 32 * u + lane;
+            const float4 q = i < w1 ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            b[4 * u] = __float_as_uint(q.x) & 0x7fffffffu;
+            b[4 * u + 1] = __float_as_uint(q.y) & 0x7fffffffu;
+            b[4 * u + 2] = __float_as_uint(q.z) & 0x7fffffffu;
+            b[4 * u + 3] = __float_as_uint(q.w) & 0x7fffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool v = it + 32 * u + lane < w1;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (v && take(b[4 * u + c])) m |= 1u << (4 * u + c);
+        }
+        const int cnt = __popc(m);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        int base = 0;
+        if (lane == 31) base = atomicAdd(n_cand, total);
+        int pos = __shfl_sync(kFull, base, 31) + incl - cnt;
+#pragma unroll
+        for (int e = 0; e < 4 * U; ++e)
+            if ((m >> e) & 1u) {
+                if (pos < kCand) cand[pos] = b[e];
+                ++pos;
+            }
+    }
+    const long long t0 = head + (nv << 2);
+    const unsigned hb = tid < head ? __float_as_uint(__ldg(x + tid)) & 0x7fffffffu : 0u;
+    agg_append(cand, n_cand, tid < head && take(hb), hb, lane);
+    const unsigned tb = t0 + tid < n ? __float_as_uint(__ldg(x + t0 + tid)) & 0x7fffffffu : 0u;
+    agg_append(cand, n_cand, t0 + tid < n && take(tb), tb, lane);
+}
+
 // ln x of a positive finite FP32 value given by its bits: x = 2^e m with m in
 // [1/sqrt 2, sqrt 2), ln x = e ln 2 (FP64, exact e) + ln m (FP32 logf, |ln m| < 0.35),
 // so the absolute error stays near 2e-8 whatever the exponent.
@@ -286,9 +347,11 @@ __device__ __forceinline__ void resolve_warp(Target& t, const Hist& h, int wb, i
     }
 }
 
-// CTAs per SM the kernel is compiled for (register budget: 3 x 512 threads x 40 registers).
+// CTAs per SM the kernel is compiled for.  Three fit the shared memory (71 KB each for 12
+// steps) but force 40 registers and spills; with the batched candidate collection two CTAs
+// (62 registers) are as fast for the arithmetic means and faster for the geometric ones.
 #ifndef ODF_MINB
-#define ODF_MINB 3
+#define ODF_MINB 2
 #endif
 __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __restrict__ kappa, int64_t N, int K,
                                                      const int64_t* __restrict__ bounds, int n_steps,
@@ -299,7 +362,7 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
     // Two phases share the dynamic shared memory: until the targets are located it holds the
     // level-1 histogram and its prefix counts; from then on (both dead) the candidates, the
-    // deeper histograms and the slot tables.  64 KB for 12 steps: three CTAs per SM.
+    // deeper histograms and the slot tables (64 KB for 12 steps).
     const Hist h1{sm, sm + kL1Bins, sm + 2 * kL1Bins};                 // [4096] each
     int* cincl = reinterpret_cast<int*>(sm + 3 * kL1Bins);             // [4096] inclusive prefix counts
     const int n2 = nslots * kL2Bins;
@@ -506,17 +569,11 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
         };
         if (collect) {
             if (lvl == 0) {
-                for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
-                    bits &= 0x7fffffffu;
-                    const bool take =
-                        valid && bits != 0u && ((tbits[bits >> (kL1Shift + 5)] >> ((bits >> kL1Shift) & 31u)) & 1u);
-                    agg_append(cand, &n_cand, take, bits, lane);
+                collect_values(x, n, cand, &n_cand, [&](unsigned bits) {
+                    return bits != 0u && ((tbits[bits >> (kL1Shift + 5)] >> ((bits >> kL1Shift) & 31u)) & 1u);
                 });
             } else {
-                for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
-                    bits &= 0x7fffffffu;
-                    agg_append(cand, &n_cand, valid && slot_of(bits) >= 0, bits, lane);
-                });
+                collect_values(x, n, cand, &n_cand, [&](unsigned bits) { return slot_of(bits) >= 0; });
             }
             __syncthreads();
             nc = min(n_cand, kCand);
