@@ -69,17 +69,12 @@ struct Target {
 
 __device__ __forceinline__ unsigned long long group_base(unsigned E) { return E >= 1 ? (1ull << 23) : 0ull; }
 
-// Visit every value of x[0..n) once.  The 16-byte-aligned body is read as float4 with
-// U loads in flight per lane before any is consumed, in one of two layouts:
-//  * CHUNKED: thread t walks one contiguous chunk, so runs of neighbouring grid points
-//    (which usually share a histogram bin) stay in one thread and merge in registers,
-//    while the lanes of a warp sit far apart and rarely hit the same bin;
-//  * otherwise warp-coalesced: each warp owns a contiguous range and lane l reads float4
-//    l, l+32, ... of it (512 contiguous bytes per warp and load).
-// The unaligned head and tail (< 4 values each) go to threads 0..3.  Every lane of a
-// warp makes the same number of calls f(bits, valid), so warp-wide collectives inside f
-// are safe.
-template <bool CHUNKED, class F>
+// Visit every value of x[0..n) once, warp-coalesced: each warp owns a contiguous range of
+// the 16-byte-aligned body and lane l reads float4 l, l+32, ... of it (512 contiguous bytes
+// per warp and load), U loads in flight per lane before any is consumed.  The unaligned
+// head and tail (< 4 values each) go to threads 0..3.  Every lane of a warp makes the same
+// number of calls f(bits, valid), so warp-wide collectives inside f are safe.
+template <class F>
 __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long long n, F&& f) {
     constexpr int U = 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -88,43 +83,22 @@ __device__ __forceinline__ void for_each_value(const float* __restrict__ x, long
     if (head > n) head = n;
     const float4* body = reinterpret_cast<const float4*>(x + head);
     const long long nv = (n - head) >> 2;
-    if (CHUNKED) {
-        const long long per = (nv + kOdfThreads - 1) / kOdfThreads;
-        const long long i0 = (long long)tid * per;
-        for (long long it = 0; it < per; it += U) {
-            float4 q[U];
+    const long long per = (((nv + kOdfWarps - 1) / kOdfWarps) + 31) & ~31ll;   // float4 per warp
+    const long long w0 = (long long)warp * per, w1 = min(w0 + per, nv);
+    for (long long it = w0; it < w0 + per; it += 32 * U) {
+        float4 q[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const long long i = i0 + it + u;
-                q[u] = (it + u < per && i < nv) ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool v = (it + u < per) && (i0 + it + u < nv);
-                f(__float_as_uint(q[u].x), v);
-                f(__float_as_uint(q[u].y), v);
-                f(__float_as_uint(q[u].z), v);
-                f(__float_as_uint(q[u].w), v);
-            }
+        for (int u = 0; u < U; ++u) {
+            const long long i = it + 32 * u + lane;
+            q[u] = i < w1 ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-    } else {
-        const long long per = (((nv + kOdfWarps - 1) / kOdfWarps) + 31) & ~31ll;   // float4 per warp
-        const long long w0 = (long long)warp * per, w1 = min(w0 + per, nv);
-        for (long long it = w0; it < w0 + per; it += 32 * U) {
-            float4 q[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const long long i = it + 32 * u + lane;
-                q[u] = i < w1 ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool v = it + 32 * u + lane < w1;
-                f(__float_as_uint(q[u].x), v);
-                f(__float_as_uint(q[u].y), v);
-                f(__float_as_uint(q[u].z), v);
-                f(__float_as_uint(q[u].w), v);
-            }
+        for (int u = 0; u < U; ++u) {
+            const bool v = it + 32 * u + lane < w1;
+            f(__float_as_uint(q[u].x), v);
+            f(__float_as_uint(q[u].y), v);
+            f(__float_as_uint(q[u].z), v);
+            f(__float_as_uint(q[u].w), v);
         }
     }
     const long long t0 = head + (nv << 2);
@@ -399,7 +373,7 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
     {
         unsigned zeros = 0;
         RunAdd run;
-        for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
+        for_each_value(x, n, [&](unsigned bits, bool valid) {
             if (!valid) return;
             bits &= 0x7fffffffu;
             zeros += bits == 0u ? 1u : 0u;
@@ -590,7 +564,7 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
             }
         } else {
             RunAdd run;
-            for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
+            for_each_value(x, n, [&](unsigned bits, bool valid) {
                 bits &= 0x7fffffffu;
                 const int q = valid ? slot_of(bits) : -1;
                 if (q < 0) return;
@@ -646,7 +620,7 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
             atomicAdd(&gacc[3][rkey], (unsigned)((rsum >> 20) & 1023u));
             atomicAdd(&gacc[4][rkey], (unsigned)(rsum >> 30));
         };
-        for_each_value<false>(x, n, [&](unsigned bits, bool valid) {
+        for_each_value(x, n, [&](unsigned bits, bool valid) {
             bits &= 0x7fffffffu;
             if (!valid || bits == 0u) return;
             int b = 0;
