@@ -85,6 +85,27 @@ def test_doppler_width_hydrogen():
     assert abs(t4.dnuD[0] / t.dnuD[0] - 2.0) < 1e-12
 
 
+def test_microturbulence():
+    # App. E: the Doppler width takes the micro-turbulent speed in quadrature with the thermal
+    # one (for hydrogen mass at 1e4 K, 12.85 km/s and 5 km/s give 13.79 km/s), and the
+    # integrated cross-section, S dnuD int H dv, does not depend on it
+    el = wl.Elements(["H", "He", "X"], np.array([1.008, 4.0026, 1.008]), np.array([13.598, 24.587, 13.598]),
+                     np.array([2.0, 1.0, 2.0]), np.array([1.0, 2.0, 1.0]), np.array([12.0, 10.93, 6.0]))
+    se, ss = np.array([2, 2], dtype=np.int32), np.array([0, 1], dtype=np.int32)
+    pop = ph.populations(1e4, 1e4, el)
+    L = one_line(500.0, 0.0, 0.0, 0)
+    g = GOLD["hydrogen_thermal_speed_1e4K_km_s"]
+    t0 = ph.line_terms(L, se, ss, el, pop, vturb=0.0)
+    t5 = ph.line_terms(L, se, ss, el, pop, vturb=5e5)
+    v5 = t5.dnuD[0] / t5.nu0[0] * 2.99792458e10 / 1e5
+    assert abs(v5 / math.hypot(g["value"], 5.0) - 1) < g["rtol"]
+    ints = []
+    for t in (t0, t5):
+        val, _ = integrate.quad(lambda v: H(v, t.a[0]), 0, np.inf, limit=400, epsabs=0, epsrel=1e-10)
+        ints.append(2 * val * t.S[0] * t.dnuD[0])
+    assert abs(ints[1] / ints[0] - 1) < 1e-8
+
+
 def test_lorentz_width():
     # for a >> 1 the profile is Lorentzian with FWHM in frequency gamma/(2 pi): ell(dnu = gamma/(4 pi)) = ell(0)/2
     el = wl.elements(5); se, ss = wl.species_table(5)
