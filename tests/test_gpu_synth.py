@@ -75,6 +75,25 @@ def test_extreme_damping_and_pressures():
         assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
 
 
+def test_microturbulence():
+    # a micro-turbulent speed of 2 km/s widens every Doppler width (context-wide setting)
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_tiny(n_lines=150, lam=(300.0, 301.0), seed=22)
+    L = w.lines()
+    se, ss = wl.species_table(w.n_metals)
+    el = wl.elements(w.n_metals)
+    ctx = binding.Context(0)
+    ctx.load_linelist(L, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P, vturb=2e5)
+    kg, kcg, _ = gpu_synth(ctx, w, np.arange(4))
+    for s in range(4):
+        pl = sy.prepare(L, se, ss, el, w.T[s], w.P[s], w.grid, w.cut, w.kc_factor, vturb=2e5)
+        k, slack, W = sy.kappa_dense(pl)
+        assert abs(kcg[s] / pl.kappa_c - 1) < 1e-5
+        bad, err, bound = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
+
+
 def test_wide_grid_far_wing_forms():
     # 9-10000 nm at R = 4000 (28k points, 14 tiles) with strongly damped rows: far wings span
     # factors of tens in wavelength, so |v| passes 1e6 on many tiles (the paired-reciprocal
