@@ -129,3 +129,24 @@ def test_geometric_below_arithmetic():
     ga = gpu_odf(x, b, W12, "arith")
     gg = check(x, b, W12, mean="geom")
     assert np.all(gg <= ga * (1 + 1e-12))
+
+
+# ---- long intervals and many ragged ones
+
+def test_long_intervals():
+    # 60 000 values per interval, two rows, both kinds of mean
+    rng = np.random.default_rng(21)
+    x = rng.lognormal(0, 4, (2, 180_000))
+    check(x, wl.equal_intervals(180_000, 3), W12)
+    check(x, wl.equal_intervals(180_000, 3), W12, mean="geom")
+
+
+def test_many_ragged_intervals():
+    # far more (row, interval) CTAs than SMs, ragged lengths and unaligned starts
+    rng = np.random.default_rng(23)
+    n = 200_001
+    x = rng.lognormal(0, 3, (2, n))
+    cuts = np.sort(rng.choice(np.arange(1, n), 1199, replace=False))
+    b = np.r_[0, cuts, n]
+    check(x, b, W12)
+    check(x, b, W12, mean="geom")
