@@ -16,4 +16,6 @@ Modules
              summation onto the grid.
   odf        sorting and sub-bin (step) means of each interval (Sect. 2.3, App. E).
   spectrum   grey atmosphere + LTE formal solution of Eq. (Ilambda).
+  bin_intensity  bin intensities from a tabulated ODF: T-P interpolation of the sub-bin
+             opacities and the width-weighted sub-bin formal solutions (Sect. 2.3, App. E).
 """
