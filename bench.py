@@ -55,7 +55,7 @@ def parse():
                    help="comma-separated table rows (T index * 25 + P index) instead of the default batch")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
-    p.add_argument("--mode", choices=["step", "serve", "batch", "precision"], default="step",
+    p.add_argument("--mode", choices=["step", "serve", "batch", "precision", "bins"], default="step",
                    help="step: the throughput benchmark; serve: Poisson request stream through the server; "
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of the request stream")
     p.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
     p.add_argument("--serve-limit", type=float, default=90.0, help="wall-clock limit of a serving run [s]")
+    p.add_argument("--bin-rays", type=int, default=8192, help="rays per step of the bin-intensity form")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -556,6 +557,93 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def bins_arm(args):
+    """Module III through ODF tables (odf_intensity): emergent bin intensities of many 1D rays
+    (grey atmospheres, 80 depths, 5 directions) from a seeded synthetic ODF table on the 57 x 25
+    T-P grid with 328 bins x 12 sub-bins.  value = rays/s with the rays resident on the device;
+    e2e adds the host->device copy of the rays and the device->host copy of the intensities."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    from oracle import bin_intensity as obi
+    nT, nP, K, ns, D = 57, 25, 328, 12, 80
+    mus = [1.0, 0.8, 0.6, 0.4, 0.2]
+    n = args.bin_rays
+    lt, lp, odf, kc, lam = wl.odf_table_synthetic(nT, nP, K, ns, seed=1005)
+    m, T, P = wl.ray_atmospheres(n, D, seed=1006)
+    ctx = binding.Context(0)
+    d_odf = torch.from_numpy(odf).cuda()
+    d_kc = torch.from_numpy(kc).cuda()
+    dm, dT, dP = (torch.from_numpy(a).cuda() for a in (m, T, P))
+    out = torch.empty((n, len(mus), K), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx.odf_intensity(lt, lp, d_odf, d_kc, lam, wl.ODF_WIDTHS_12, dm, dT, dP, mus, out, stream=st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ctx.profile_enable(True)
+    ctx.profile_read(binding.KERNEL_BINS)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 30)   # a timed region of about a second for the clock samples
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    k_ms, k_n = ctx.profile_read(binding.KERNEL_BINS)
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    # end to end: rays from pinned host memory, intensities back to pinned memory
+    hm, hT, hP = (torch.from_numpy(a).pin_memory() for a in (m, T, P))
+    hout = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        dm.copy_(hm, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        dP.copy_(hP, non_blocking=True)
+        step()
+        hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dm.copy_(hm, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        dP.copy_(hP, non_blocking=True)
+        step()
+        hout.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    # oracle baseline on a bounded sample of rays
+    t0 = time.perf_counter()
+    done = 0
+    while time.perf_counter() - t0 < 10.0 and done < 64:
+        obi.bin_intensity(odf.reshape(nT, nP, K, ns), kc.reshape(nT, nP).astype(np.float64), lt, lp, lam,
+                          wl.ODF_WIDTHS_12, m[done], T[done], P[done], mus)
+        done += 1
+    t_cpu = time.perf_counter() - t0
+    updates = n * K * ns * (D - 1) * len(mus)
+    out_line = {"mode": "bins", "metric": "rays/s (bin intensities from an ODF table)", "value": n / (ms / 1e3),
+                "unit": "rays/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"odf_table_57x25x{K}x{ns}_rays{n}_D{D}_mu5", "rays": n, "depth": D, "bins": K,
+                           "sub_bins": ns, "mu": len(mus), "table_bytes": int(odf.nbytes + kc.nbytes)},
+                "bin_intensities_per_s": n * K / (ms / 1e3),
+                "layer_updates_per_s": updates / (ms / 1e3),
+                "kernel_ms": k_ms / max(k_n, 1),
+                "e2e": {"value": n / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": int(3 * m.nbytes),
+                        "d2h_bytes_per_step": int(hout.numel() * 4)},
+                "cpu_baseline": {"value": done / t_cpu, "unit": "rays/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{done} rays of the same table"},
+                "gpu_launches": 3 * steps, "clocks": clk}
+    print(json.dumps(out_line), flush=True)
+
+
 def precision_arm(args):
     """Precision study: a 1e8-line list (same distributions, 9-10000 nm) on a 6 x 5 (T, P)
     subset of the table, synthesised on a 1 nm slice (300-301 nm at R = 2e6, every line of the
@@ -646,6 +734,9 @@ def main():
         return
     if args.mode == "batch":
         batch_arm(args)
+        return
+    if args.mode == "bins":
+        bins_arm(args)
         return
     if args.mode == "serve":
         serve_arm(args)

@@ -238,6 +238,49 @@ int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_lgrid* win,
                    int32_t n_mu, const double* mu, float* I_out,
                    const mpsa_synth_opts* opts, void* stream);
 
+/* An ODF table of one composition on a T-P grid: the sub-bin mean line opacities of
+ * build_odf for the grid's points and the continuum opacity of each point. */
+typedef struct {
+    int32_t nT, nP;           /* grid: table row r = iT * nP + iP */
+    const double* log10_T;    /* host [nT], strictly increasing */
+    const double* log10_P;    /* host [nP], strictly increasing (P in dyn cm^-2) */
+    int32_t K;                /* bins */
+    int32_t n_steps;          /* sub-bins per bin, 1..32 */
+    const double* odf;        /* device double[nT * nP][K][n_steps]: sub-bin mean line
+                                 opacity [cm^2 g^-1] (build_odf's output for rows r) */
+    const float* kappa_c;     /* device float[nT * nP]: continuum opacity [cm^2 g^-1]
+                                 (synth_opacity's kappa_c_out for rows r), > 0 */
+    const double* lam_c_nm;   /* host [K]: bin centre wavelengths [nm] */
+    const double* widths;     /* host [n_steps]: sub-bin widths as fractions of the bin,
+                                 positive, summing to 1 */
+} mpsa_odf_table;
+
+/*
+ * odf_intensity -- emergent bin intensities of many 1D atmospheres from an ODF table
+ * (module III through ODFs; paper Sect. 2.3 and App. E):
+ *   I_bin,k(mu) = sum_s w_s I_lambda_c,k(kappa_c + kappa_s,k; mu).
+ * At every depth of a ray the sub-bin opacities kappa_s,k and the continuum are
+ * interpolated bilinearly in (log10 T, log10 P) on the table grid (coordinates clamped
+ * to the grid's edges); per sub-bin, tau follows by the trapezoid rule in column mass
+ * and I by the formal solution of synth_spectrum (S = B_lambda(T) at the bin centre,
+ * diffusion lower boundary); the bin intensity is the width-weighted sum.  FP32
+ * arithmetic; the table is read in FP64 and rounded per value.
+ *   tab (host struct): the table (odf and kappa_c on the device, the rest on the host);
+ *     nT * nP * K * n_steps below 2^31 values.
+ *   n_rays (1..65535), n_depth (2..256): rays of n_depth points each, top down.
+ *   m, T, P (device, double[n_rays][n_depth]): column mass [g cm^-2] (positive,
+ *     strictly increasing), T [K] and P [dyn cm^-2] (positive, finite).
+ *   n_mu (1..16), mu[n_mu] (host): direction cosines in (0, 1].
+ *   I_out (device, float[n_rays][n_mu][K]).
+ *   ray_status (device, int32[n_rays], may be NULL): 0 for a valid ray; 1 where its m, T
+ *     or P break the rules above, in which case its I_out is NaN.
+ * The ray arrays are checked on the device (no synchronisation).  Stream-ordered.
+ * Errors: MPSA_EINVAL (host arguments), MPSA_ENOMEM, MPSA_ECUDA.
+ */
+int odf_intensity(mpsa_ctx* ctx, const mpsa_odf_table* tab, int32_t n_rays, int32_t n_depth,
+                  const double* m, const double* T, const double* P, int32_t n_mu, const double* mu,
+                  float* I_out, int32_t* ray_status, void* stream);
+
 /*
  * Batched form: many rows on several grids in one persistent, graph-captured
  * launch (the paper's method, Eq. l_nu_line + App. E, over a heterogeneous set of
@@ -348,14 +391,15 @@ void mpsa_server_destroy(mpsa_server* s);
 /*
  * Kernel timing for measurement tools (not part of the method).  While enabled,
  * the library records a CUDA event pair on the launching stream around each
- * launch of its two dominant kernels: MPSA_KERNEL_PROFILE (the profile kernel
- * of synth_opacity / synth_spectrum) and MPSA_KERNEL_ODF (the kernel of
- * build_odf).  mpsa_profile_read waits for the recorded events, returns the
+ * launch of its dominant kernels: MPSA_KERNEL_PROFILE (the profile kernel
+ * of synth_opacity / synth_spectrum), MPSA_KERNEL_ODF (the kernel of
+ * build_odf) and MPSA_KERNEL_BINS (the kernel of odf_intensity).  mpsa_profile_read waits for the recorded events, returns the
  * summed device time [ms] and launch count of one kernel, and clears its list.
  * Do not enable while capturing a CUDA graph.
  */
 #define MPSA_KERNEL_PROFILE 0
 #define MPSA_KERNEL_ODF     1
+#define MPSA_KERNEL_BINS    2
 int mpsa_profile_enable(mpsa_ctx* ctx, int enable);
 int mpsa_profile_read(mpsa_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
 

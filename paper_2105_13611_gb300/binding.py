@@ -23,9 +23,10 @@ EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "m
             "mpsa_profile_enable", "mpsa_profile_read", "build_odf_noalloc",
             "mpsa_server_create", "mpsa_server_submit", "mpsa_server_wait", "mpsa_server_get_stats",
             "mpsa_server_destroy", "mpsa_server_cancel_queued",
-            "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy", "mpsa_voigt"]
+            "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy", "mpsa_voigt",
+            "odf_intensity"]
 REQ_SPECTRUM, REQ_ODF = 1, 2
-KERNEL_PROFILE, KERNEL_ODF = 0, 1
+KERNEL_PROFILE, KERNEL_ODF, KERNEL_BINS = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -66,6 +67,12 @@ class BatchGroup(C.Structure):
                 ("kappa_c_out", C.c_void_p), ("evals_out", C.c_void_p), ("K", C.c_int32),
                 ("bounds", C.POINTER(C.c_int64)), ("n_steps", C.c_int32), ("widths", _dp), ("odf_out", C.c_void_p),
                 ("mean_kind", C.c_int32)]
+
+
+class OdfTable(C.Structure):
+    _fields_ = [("nT", C.c_int32), ("nP", C.c_int32), ("log10_T", _dp), ("log10_P", _dp), ("K", C.c_int32),
+                ("n_steps", C.c_int32), ("odf", C.c_void_p), ("kappa_c", C.c_void_p), ("lam_c_nm", _dp),
+                ("widths", _dp)]
 
 
 class BatchInfo(C.Structure):
@@ -111,6 +118,9 @@ def load_library(path: str = LIB_PATH):
                               C.c_int32, vp, vp]
     lib.synth_spectrum.argtypes = [vp, C.POINTER(Atmos), C.POINTER(LGrid), C.c_int32, _dp, vp,
                                    C.POINTER(SynthOpts), vp]
+    lib.odf_intensity.argtypes = [vp, C.POINTER(OdfTable), C.c_int32, C.c_int32, vp, vp, vp, C.c_int32, _dp, vp, vp,
+                                  vp]
+    lib.odf_intensity.restype = C.c_int
     lib.build_odf_noalloc.argtypes = [C.c_int32, vp, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.c_int32,
                                       _dp, C.c_int32, vp, vp]
     lib.build_odf_noalloc.restype = C.c_int
@@ -220,7 +230,7 @@ class Context:
         _check(self.lib.mpsa_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self, kernel):
-        """(total device ms, launches) of KERNEL_PROFILE or KERNEL_ODF since the last read."""
+        """(total device ms, launches) of KERNEL_PROFILE, KERNEL_ODF or KERNEL_BINS since the last read."""
         ms = C.c_double()
         n = C.c_int64()
         _check(self.lib.mpsa_profile_read(self.h, kernel, C.byref(ms), C.byref(n)))
@@ -282,6 +292,27 @@ class Context:
         o = opts if opts is not None else make_opts()
         _check(self.lib.synth_spectrum(self.h, C.byref(a), C.byref(g), len(mu), _ptr(mu, C.c_double), _dev(I_out),
                                        C.byref(o), _stream(stream)))
+
+
+    def odf_intensity(self, log10_T, log10_P, odf, kappa_c, lam_c_nm, widths, m, T, P, mus, I_out,
+                      ray_status=None, stream=None):
+        """Bin intensities of many rays from an ODF table (odf_intensity in include/mpsa.h).
+
+        log10_T [nT], log10_P [nP], lam_c_nm [K], widths [n_steps], mus: host arrays;
+        odf (float64 [nT*nP][K][n_steps]), kappa_c (float32 [nT*nP]), m, T, P (float64
+        [n_rays][n_depth]), I_out (float32 [n_rays][n_mu][K]) and ray_status (int32 [n_rays]
+        or None): CUDA tensors."""
+        lt = _arr(log10_T, np.float64)
+        lp = _arr(log10_P, np.float64)
+        lam = _arr(lam_c_nm, np.float64)
+        w = _arr(widths, np.float64)
+        mu = _arr(mus, np.float64)
+        K, ns = int(odf.shape[-2]), int(odf.shape[-1])
+        tab = OdfTable(len(lt), len(lp), _ptr(lt, C.c_double), _ptr(lp, C.c_double), K, ns, _dev(odf),
+                       _dev(kappa_c), _ptr(lam, C.c_double), _ptr(w, C.c_double))
+        n_rays, n_depth = int(m.shape[0]), int(m.shape[1])
+        _check(self.lib.odf_intensity(self.h, C.byref(tab), n_rays, n_depth, _dev(m), _dev(T), _dev(P), len(mu),
+                                      _ptr(mu, C.c_double), _dev(I_out), _dev(ray_status), _stream(stream)))
 
 
 class Server:

@@ -274,7 +274,7 @@ int mpsa_profile_enable(mpsa_ctx* c, int enable) {
 }
 
 int mpsa_profile_read(mpsa_ctx* c, int kernel, double* total_ms, int64_t* launches) {
-    if (!c || !total_ms || !launches || kernel < 0 || kernel > 1) return fail(MPSA_EINVAL, "mpsa_profile_read: bad argument");
+    if (!c || !total_ms || !launches || kernel < 0 || kernel > 2) return fail(MPSA_EINVAL, "mpsa_profile_read: bad argument");
     auto& v = c->prof_ev[kernel];
     double tot = 0.0;
     int64_t n = 0;

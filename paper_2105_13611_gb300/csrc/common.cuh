@@ -97,7 +97,7 @@ struct mpsa_ctx {
     std::vector<double> h_abund;     // [n_comp][n_el]
     // kernel timing (mpsa_profile_enable)
     bool prof = false;
-    std::vector<cudaEvent_t> prof_ev[2];   // start/stop pairs per kernel
+    std::vector<cudaEvent_t> prof_ev[3];   // start/stop pairs per kernel
 };
 
 namespace mpsa {

@@ -169,6 +169,34 @@ def grey_atmosphere(D: int, Teff: float, logg: float, log_tau_top=-6.8, log_tau_
     return m, T, P
 
 
+def odf_table_synthetic(nT: int, nP: int, K: int, n_steps: int, seed: int, lam_lo_nm=9.0, lam_hi_nm=10000.0):
+    """Seeded synthetic ODF table on the DFSYNTHE-style T-P grid (tp_grid_dfsynthe with nT x nP
+    points): returns (log10_T [nT], log10_P [nP], odf [nT*nP][K][n_steps] (per grid point and
+    bin a median 10^U(-2, 2) times 10^N(0, 1) spreads, sorted ascending over the sub-bins),
+    kappa_c [nT*nP] float32 = 10^U(-3, 0), lam_c_nm [K] (centres of K log-equal bins))."""
+    rng = np.random.default_rng(seed)
+    T, P = tp_grid_dfsynthe(nT, nP)
+    lt = np.log10(T.reshape(nT, nP)[:, 0]).copy()
+    lp = np.log10(P.reshape(nT, nP)[0, :]).copy()
+    base = 10.0 ** rng.uniform(-2.0, 2.0, (nT * nP, K, 1))
+    odf = np.sort(base * 10.0 ** rng.normal(0.0, 1.0, (nT * nP, K, n_steps)), axis=-1)
+    kc = (10.0 ** rng.uniform(-3.0, 0.0, nT * nP)).astype(np.float32)
+    edges = np.exp(np.linspace(math.log(lam_lo_nm), math.log(lam_hi_nm), K + 1))
+    return lt, lp, odf, kc, 0.5 * (edges[:-1] + edges[1:])
+
+
+def ray_atmospheres(n_rays: int, D: int, seed: int):
+    """n_rays grey atmospheres of D depths (Teff ~ U(3500, 12000) K, log g ~ U(1, 5), the
+    spectrum workload's model), as float64 arrays [n_rays][D] of m, T, P."""
+    rng = np.random.default_rng(seed)
+    m = np.empty((n_rays, D))
+    T = np.empty((n_rays, D))
+    P = np.empty((n_rays, D))
+    for r in range(n_rays):
+        m[r], T[r], P[r] = grey_atmosphere(D, rng.uniform(3500.0, 12000.0), rng.uniform(1.0, 5.0))
+    return m, T, P
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------
