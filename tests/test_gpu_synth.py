@@ -96,8 +96,8 @@ def test_microturbulence():
 
 def test_wide_grid_far_wing_forms():
     # 9-10000 nm at R = 4000 (28k points, 14 tiles) with strongly damped rows: far wings span
-    # factors of tens in wavelength, so |v| passes 1e6 on many tiles (the paired-reciprocal
-    # far form) as well as staying below it (the three-point form)
+    # factors of tens in wavelength, so |v| passes 1e6 on many tiles as well as staying below
+    # it (the two lists of the paired-reciprocal far form) and passes 1e9 on some (the y form)
     w = wl.config_tiny(n_lines=80, lam=(9.0, 10000.0), R=4000.0, seed=21)
     w.T = np.array([3000.0, 6000.0, 12000.0, 40000.0])
     w.P = np.array([1e8, 1e7, 1e8, 1e6])
@@ -150,3 +150,45 @@ def test_precision_variants_against_oracle():
         m = slack == 0
         rel64 = np.abs(res[2][s][m].astype(np.float64) - k[m]) / (k[m] + pl.kappa_c)
         assert rel64.max() < 1e-7        # FP32 output rounding bounds it
+
+
+def test_table_workload_sampled():
+    # the benchmark's own workload and launch: 5e6 lines over 9-10000 nm at R = 2e6 (14.0 M
+    # points), the 8 (T, P) rows of one bench step in one synth_opacity call, then build_odf
+    # over the 328 intervals.  The oracle evaluates sampled points of two rows one by one
+    # (random points and the cores of the strongest lines) and the ODF of sampled intervals on
+    # the same FP32 opacity.
+    import torch
+    from oracle import odf as od
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    ctx, L = gpu_context(w)
+    rows = [277, 879, 232, 964, 1354, 1044, 1321, 297]
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    kap = torch.empty((len(rows), N), dtype=torch.float32, device="cuda")
+    kc = torch.empty(len(rows), dtype=torch.float32, device="cuda")
+    ctx.synth_opacity(w.grid, rows, kap, kc)
+    b = wl.equal_intervals(N, w.n_intervals)
+    odf = torch.empty((len(rows), w.n_intervals, 12), dtype=torch.float64, device="cuda")
+    ctx.build_odf(kap, b, w.widths, odf)
+    torch.cuda.synchronize()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    rng = np.random.default_rng(5)
+    lnq = np.log1p(1 / w.grid.R)
+    for i in (5, 0):   # row 1044 (strong damping, far wings) and row 277
+        r = rows[i]
+        pl = sy.prepare(L, se, ss, el, w.T[r], w.P[r], w.grid, w.cut, w.kc_factor)
+        assert abs(float(kc[i]) / pl.kappa_c - 1) < 1e-5
+        strong = np.argsort(pl.kappa0)[-2:]
+        centres = np.round(np.log(L.lam_nm[strong] / w.grid.lam0_nm) / lnq).astype(np.int64)
+        js = np.unique(np.clip(np.r_[rng.integers(0, N, 4), centres, centres + 5], 0, N - 1))
+        kg = kap[i, torch.from_numpy(js).cuda()].cpu().numpy()
+        ko, so = sy.kappa_at(pl, js)
+        bad, err, bound = opacity_violations(kg, ko, pl.kappa_c, so)
+        assert len(bad) == 0, (r, js[bad[:5]], rel_report(kg, ko, pl.kappa_c))
+        og = odf[i].cpu().numpy()
+        for k in rng.choice(w.n_intervals, 4, replace=False):
+            x = kap[i, int(b[k]):int(b[k + 1])].cpu().numpy().astype(np.float64)
+            o = od.odf(x, [0, len(x)], w.widths)[0]
+            assert np.all(np.abs(og[k] - o) <= 1e-5 * np.abs(o) + 1e-300), (r, k)
