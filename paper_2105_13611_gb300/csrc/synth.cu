@@ -498,7 +498,7 @@ constexpr int kFlChk = 1 << 10;      // points near the cut: test s_rel H >= 1
 constexpr int kFlAlt = 1 << 11;      // far: "y" form; near: expm1 series for v
 constexpr int kFlFull = 1 << 12;     // the window covers every slot of the tile
 constexpr int kFlRat = 1 << 13;      // far: rational form sk / (|z|^2 - 3/2)
-constexpr int kFlSmall = 1 << 14;    // far, rational: |v| < 1e6 on the tile (a list of its own)
+constexpr int kFlScaled = 1 << 14;   // far, rational: the line may be evaluated in units of sk (far_rat_pairs_scaled)
 
 struct NearRec {
     float cf, f, klnq, a, srel, kv;
@@ -567,9 +567,9 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 // thread's points are taken as pairs (2j, 2j+1): v and D = v^2 + a^2 - 3/2 of both points
 // in one packed FFMA each, r = 1/(D_0 D_1) and, with sr = sk r,
 // sk/D_0 = sr D_1 and sk/D_1 = sr D_0 (about two ulps) in one packed FFMA into the pair's
-// partial sums, held as {part_{2j+1}, part_{2j}}.  Per evaluation: 1.5 instructions on the
-// FMA pipe (4 lane operations) and half a reciprocal.  D_0 D_1 < 1e36 stays finite because
-// the form is used only where |v| < 1e9 on the whole tile.
+// partial sums, held as {part_{2j+1}, part_{2j}}.  Per pair: three packed FFMAs and two
+// FMULs on the FMA pipe (8 lane operations) and one reciprocal.  D_0 D_1 < 1e36 stays finite
+// because the form is used only where |v| < 1e9 on the whole tile.
 // u = {kv B, kv B, kv E1, kv E1}, w = {a^2 - 3/2, a^2 - 3/2, sk, sk} (duplicated so that
 // each operand pair comes straight from one 16-byte shared-memory load).
 template <int PTS>
@@ -586,6 +586,29 @@ __device__ __forceinline__ void far_rat_pairs(const float4 u, const float4 w, co
         float2 acc = make_float2(part[2 * j + 1], part[2 * j]);
         const float sr = sk * rcp_approx(P01);
         acc = ffma2(make_float2(sr, sr), D, acc);
+        part[2 * j + 1] = acc.x;
+        part[2 * j] = acc.y;
+    }
+}
+
+// plain line in the rational form, in units of sk: with v' = v / sqrt(sk) and
+// D' = v'^2 + (a^2 - 3/2)/sk = D/sk, the contribution sk/D is 1/D', so the factor sk leaves
+// the inner loop: r = 1/(D'_0 D'_1), 1/D'_0 = r D'_1, 1/D'_1 = r D'_0.  Per pair: three
+// packed FFMAs and one FMUL (7 lane operations) and one reciprocal.  Used for lines with
+// sk <= 1e18 D_min and |v|_max <= 1e9 sqrt(sk) on the tile, so that every D' lies in
+// [1e-18, 1e18] and the products stay normal FP32 numbers.
+// u = {B', B', E', E'} = {kv B, kv B, kv E1, kv E1} / sqrt(sk), w = {c', c', -, -}.
+template <int PTS>
+__device__ __forceinline__ void far_rat_pairs_scaled(const float4 u, const float4 w, const float (&G)[PTS],
+                                                     float (&part)[PTS]) {
+    static_assert(PTS % 2 == 0, "points are taken in pairs");
+    const float2 B2 = make_float2(u.x, u.y), E2 = make_float2(u.z, u.w), C2 = make_float2(w.x, w.y);
+#pragma unroll
+    for (int j = 0; j < PTS / 2; ++j) {
+        const float2 v = ffma2(make_float2(G[2 * j], G[2 * j + 1]), B2, E2);
+        const float2 D = ffma2(v, v, C2);
+        const float r = rcp_approx(D.x * D.y);
+        const float2 acc = ffma2(make_float2(r, r), D, make_float2(part[2 * j + 1], part[2 * j]));
         part[2 * j + 1] = acc.x;
         part[2 * j] = acc.y;
     }
@@ -697,9 +720,11 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                         const float zmin2 = fmaf(vmin, vmin, A);
                         if (zmin2 * zmin2 >= 1.0e6f * fmaf(2.f, A, 2.f)) {
                             fa = make_float4(kv * B, kv * E1, A - 1.5f, sk);
+                            // every D/sk of the tile within [1e-18, 1e18]: the form in units of sk
+                            const bool scaled = sk <= 1.0e18f * (zmin2 - 1.5f) && vmax <= 1.0e9f * sqrtf(sk);
                             fb = make_float4(0.f, 0.f,
                                              __int_as_float(flags | kFlRat | (yform ? kFlAlt : 0) |
-                                                            (vmax < 1.0e6f ? kFlSmall : 0)),
+                                                            (scaled ? kFlScaled : 0)),
                                              0.f);
                         } else {
                             fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
@@ -722,20 +747,21 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                     }
                 }
             }
-            // far lines are compacted into five lists: plain rational with |v| < 1e6 and with
-            // 1e6 <= |v| < 1e9 on the tile, plain "exact" and plain "y" forms, and masked
-            // (partial coverage or cut test), so the hot loops dispatch nothing; near lines into
-            // a sixth.  Both rational lists take the same packed form; keeping them apart
-            // measured 1.5 % faster on the 8-row table step than one merged list (the register
-            // allocation of the kernel differs)
+            // far lines are compacted into five lists: plain rational in units of sk, plain
+            // rational with two points per reciprocal (the few lines the scaled form cannot
+            // take), plain "exact" and plain "y" forms, and masked (partial coverage or cut
+            // test), so the hot loops dispatch nothing; near lines into a sixth
             constexpr int kNearCat = 5;
             int cat = -1;
             if (isFar) {
                 const int fl = __float_as_int(fb.z);
                 const bool plain = (fl & kFlFull) && !(fl & kFlChk);
                 // rational lines with |v| >= 1e9 somewhere take the single-reciprocal masked path
+                // rational lines: in units of sk where allowed (list 0), else two points per
+                // reciprocal where |v| < 1e9 (list 1), else the single-reciprocal masked path
                 cat = !plain ? 4
-                             : ((fl & kFlRat) ? ((fl & kFlAlt) ? 4 : ((fl & kFlSmall) ? 0 : 1)) : ((fl & kFlAlt) ? 3 : 2));
+                             : ((fl & kFlRat) ? ((fl & kFlScaled) ? 0 : ((fl & kFlAlt) ? 4 : 1))
+                                              : ((fl & kFlAlt) ? 3 : 2));
             } else if (isNear) {
                 cat = kNearCat;
             }
@@ -764,7 +790,11 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                 for (int q = 0; q < kNearCat - 1; ++q)
                     if (q < cat) base2 += tot[q];
                 const int p = base2 + off + __popc(bm & lt);
-                if (cat <= 1) {
+                if (cat == 0) {
+                    const float rs = 1.f / sqrtf(fa.w), c1 = fa.z / fa.w;
+                    sFarA[p] = make_float4(fa.x * rs, fa.x * rs, fa.y * rs, fa.y * rs);
+                    sFarB[p] = make_float4(c1, c1, 0.f, 0.f);
+                } else if (cat <= 1) {
                     sFarA[p] = make_float4(fa.x, fa.x, fa.y, fa.y);
                     sFarB[p] = make_float4(fa.z, fa.z, fa.w, fa.w);
                 } else {
@@ -783,11 +813,11 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
                 // dependency chains per point for the scheduler
                 for (; r + 1 < tot[0]; r += 2) {
                     const float4 ua = sFarA[r], wa = sFarB[r], ub = sFarA[r + 1], wb = sFarB[r + 1];
-                    far_rat_pairs<PTS>(ua, wa, G, part);
-                    far_rat_pairs<PTS>(ub, wb, G, part);
+                    far_rat_pairs_scaled<PTS>(ua, wa, G, part);
+                    far_rat_pairs_scaled<PTS>(ub, wb, G, part);
                 }
                 if (r < tot[0]) {
-                    far_rat_pairs<PTS>(sFarA[r], sFarB[r], G, part);
+                    far_rat_pairs_scaled<PTS>(sFarA[r], sFarB[r], G, part);
                     ++r;
                 }
                 const int e1 = tot[0] + tot[1];
