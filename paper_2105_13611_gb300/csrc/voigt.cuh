@@ -89,18 +89,23 @@ __device__ __forceinline__ float voigt_far(float V, float A, float ka) {
     return ka * y * fmaf(4.f, y, 2.f) * fmaf(e, e - 1.f, 1.f);
 }
 
-// mid tier (five continued-fraction levels).
+// mid tier (five continued-fraction levels).  The fraction t <- z - (k/2)/t is carried
+// bottom-up as t = P/Q, (P, Q) <- (z P - (k/2) Q, P), so that one reciprocal serves all five
+// levels: H = Re(i Q/P)/sqrt(pi) = (Q_r P_i - Q_i P_r) / (sqrt(pi) |P|^2).  For 36 <= |z|^2 <
+// 1600, |P| <= |z|^6 < 5e9 and |P|^2 stays inside FP32.
 __device__ __forceinline__ float voigt_mid(float v, float a) {
-    float tr = v, ti = a;
+    float pr = v, pi = a, qr = 1.f, qi = 0.f;
 #pragma unroll
     for (int k = 5; k >= 1; --k) {
         const float c = 0.5f * (float)k;
-        float cm = c * rcp_approx(fmaf(tr, tr, ti * ti));
-        float ntr = fmaf(-cm, tr, v);
-        ti = fmaf(cm, ti, a);
-        tr = ntr;
+        const float npr = fmaf(v, pr, fmaf(-a, pi, -c * qr));
+        const float npi = fmaf(v, pi, fmaf(a, pr, -c * qi));
+        qr = pr;
+        qi = pi;
+        pr = npr;
+        pi = npi;
     }
-    float h = kInvSqrtPi * ti * rcp_approx(fmaf(tr, tr, ti * ti));
+    float h = kInvSqrtPi * fmaf(qr, pi, -qi * pr) * rcp_approx(fmaf(pr, pr, pi * pi));
     if (a < 1e-2f) h += expf(-v * v);
     return h;
 }
