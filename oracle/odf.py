@@ -3,7 +3,7 @@
 Sect. 2.3 and App. E of the paper: the high-resolution opacity of each
 wavelength interval (bin) is sorted in ascending order, the sorted profile is
 split into sub-bins whose widths are given fractions of the bin, and each
-sub-bin is replaced by its mean.  Readings (DESIGN.md):
+sub-bin is replaced by its mean.  Readings:
   * every grid point of an interval carries equal weight (on a log-lambda grid
     the points are equally spaced in ln lambda);
   * sub-bin boundaries fall at cumulative width fractions c_s = w_1 + ... + w_s,

@@ -5,7 +5,7 @@ equations with the electron density found iteratively from particle and charge
 conservation (App. A), and the line absorption coefficient of Eq. (l_nu_line)
 with the Doppler width of App. E.
 
-Readings where the paper is silent (all stated in the design doc):
+Readings where the paper is silent:
   * single ionisation only (stages I, II) with fixed partition functions;
   * the gas is H, He and the metals of the element table (no molecules);
   * total damping gamma = 10^lgR + 10^lgS * n_e + 10^lgW * n_HI (per-perturber

@@ -4,7 +4,7 @@ Eq. (Ilambda) of the paper: I_lambda(mu) = integral_0^inf S_lambda exp(-tau_lamb
 with S_lambda = B_lambda(T) in LTE without scattering (Sect. 2).  The paper's
 module III uses Feautrier / iterative solvers with scattering (App. D); the
 synthetic spectrum workload reduces this to the plain integral, evaluated layer
-by layer with S linear in tau inside each layer (readings in the design doc):
+by layer with S linear in tau inside each layer:
 
   tau_0 = kappa_0 m_0,  tau_{d+1} = tau_d + (kappa_d + kappa_{d+1}) (m_{d+1} - m_d)/2,
   bottom: I_{D-1} = S_{D-1} + mu dS/dtau (diffusion approximation),

@@ -1,7 +1,6 @@
 // FP32 Voigt function H(v, a) = Re w(v + i a) for the profile of Eq. (l_nu_line).
 //
-// Three tiers, chosen per point by |z|^2 = v^2 + a^2 (the reasoning and the
-// measured error bounds are in the design doc):
+// Three tiers, chosen per point by |z|^2 = v^2 + a^2:
 //
 //  far   |z|^2 >= 1600: the one-level Laplace continued fraction
 //        w ~ (i/sqrt(pi)) / (z - 1/(2z)) with its real part written out:
