@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
     } else if (warp == 1 && lane < nt) {
         // each target's level-1 bin: the first bin whose inclusive count exceeds its rank
         Target t;
-        // u = c_s n rounded to FP64 exactly as written (no fused multiply-add), as the reference does
+        // u = c_s n as one rounded FP64 product (no fused multiply-add), so that the rank is
+        // the floor of the correctly rounded product whatever the compiler contracts
         t.k = (long long)floor(__dmul_rn(cw[lane + 1], (double)n));
         t.total = t.k >= n;
         t.slot = -1;
