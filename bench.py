@@ -35,12 +35,13 @@ import workloads as wl  # noqa: E402
 
 METRIC = "Voigt line-evals/s (line-by-line opacity synthesis + ODF binning)"
 UNIT = "line-evals/s"
-# FP32 operations of one far-wing profile evaluation in the paired rational form (the form
-# that takes most evaluations): v = fma(G, kv B, kv E1); D = fma(v, v, a^2 - 3/2); per pair
-# of points P = D0 D1 and sr = sk (1/P) (half an FMUL each), accumulate fma(sr, D_other, sum):
-# 3 FFMA + 1 FMUL = 7 flop, plus half a reciprocal on the special-function unit (not counted).
-FLOP_PER_EVAL = 7
-SMS = 152
+# FP32 operations of one far-wing profile evaluation in the form that takes 97-99.6 % of the
+# evaluations of the table rows (plain rational form in units of sk, two points per
+# reciprocal, packed FP32): per pair of points {v0, v1} = fma(G, B', E'), {D0, D1} =
+# fma(v, v, c') and {s1, s0} += r {D0, D1} are three packed FFMAs (12 flop) and
+# r = rcp(D0 D1) one FMUL (1 flop): 13 flop per pair, 6.5 per evaluation, plus half a
+# reciprocal on the special-function unit (not counted).
+FLOP_PER_EVAL = 6.5
 FP32_LANES_PER_SM = 128
 
 
@@ -77,13 +78,20 @@ def parse():
 TABLE_ROWS = [277, 879, 232, 964, 1354, 1044, 1321, 297]
 
 
-def batch_points(rank: int, B: int):
-    """The first B rows of TABLE_ROWS; rank r shifts every row's temperature index by r."""
+def batch_points(rank: int, B: int, world: int = 1):
+    """Rows of `rank` among `world` ranks, B per rank, through the row-sharding helper: the
+    first B rows of TABLE_ROWS, each with its temperature neighbours T index +- k (k < world)
+    as rows of the same cost class, interleaved so that round-robin sharding gives rank k
+    every class's k-th neighbour (the same cost mix on every rank; rank 0 takes TABLE_ROWS)."""
+    from paper_2105_13611_gb300.sharding import rows_for_rank
     if not 1 <= B <= len(TABLE_ROWS):
         raise ValueError(f"--batch must be 1..{len(TABLE_ROWS)}")
-    rows = np.array(TABLE_ROWS[:B], dtype=np.int64)
-    ti, pi = rows // 25, rows % 25
-    return (((ti + rank) % 57) * 25 + pi).astype(np.int32)
+    base = np.array(TABLE_ROWS[:B], dtype=np.int64)
+    ti, pi = base // 25, base % 25
+    # order[j * world + k] = k-th temperature neighbour of row j (downwards near the hot end)
+    step = lambda t: 1 if t + world - 1 <= 56 else -1
+    order = np.array([(t + step(t) * k) * 25 + p for t, p in zip(ti, pi) for k in range(world)], dtype=np.int64)
+    return rows_for_rank(len(order), rank, world, order=order)
 
 
 class Clocks:
@@ -219,7 +227,7 @@ def reference_arm(args):
     if rank != 0:
         return
     w = wl.config_table() if args.workload == "table" else wl.config_small()
-    pts = batch_points(0, args.batch) if args.workload == "table" else np.arange(len(w.T))
+    pts = batch_points(0, args.batch, 1) if args.workload == "table" else np.arange(len(w.T))
     T, P = float(w.T[pts[0]]), float(w.P[pts[0]])
     per_step = max(5.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     pool, n = oracle_pool(args.workload)
@@ -288,7 +296,7 @@ def native_arm(args):
     if args.rows:
         sel = np.array([int(x) for x in args.rows.split(",")], dtype=np.int32)
     else:
-        sel = batch_points(rank, args.batch) if args.workload == "table" else np.arange(len(w.T), dtype=np.int32)
+        sel = batch_points(rank, args.batch, world) if args.workload == "table" else np.arange(len(w.T), dtype=np.int32)
     B = len(sel)
     stream = torch.cuda.current_stream()
     kap = torch.empty((B, N), dtype=torch.float32, device=dev)
@@ -378,15 +386,16 @@ def native_arm(args):
         return
 
     hbm, sm_max, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     tiles_avg = tiles_ms / max(tiles_n, 1)
     evals_per_launch = evals_rank / max(tiles_n, 1)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
     achieved = evals_per_launch * FLOP_PER_EVAL / (tiles_avg / 1e3) / 1e12
     traffic = measured_traffic("k_tiles", ["synth.cu", "voigt.cuh", "common.cuh"], sel)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_tiles (profile synthesis)",
-                "peak_kind": f"FP32 FMA peak {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
-                "flop_per_eval": FLOP_PER_EVAL, "avg_launch_ms": tiles_avg, "launches": tiles_n}
+                "peak_kind": f"FP32 FMA peak {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
+                "sms": sms, "flop_per_eval": FLOP_PER_EVAL, "avg_launch_ms": tiles_avg, "launches": tiles_n}
     odf_avg = odf_ms / max(odf_n, 1)
     odf_bytes = B * N * 4 + B * K * 12 * 8
     roofline_odf = {"bound": "hbm", "achieved": odf_bytes / (odf_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",

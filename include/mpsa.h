@@ -177,6 +177,7 @@ int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const in
  *     width, the paper's default in Sect. 2.3; a sub-bin whose rank range
  *     reaches into zero values has geometric mean 0).
  *   odf_out (device, double[n_rows][K][n_steps]).
+ *   n_rows: 1..65535 rows per call (one launch; split larger tables).
  * Order statistics are found by a 4-level radix multi-select (12, 7, 6 and 6
  * bits) on the FP32 bit patterns with exact integer partial sums; only the final
  * cross-exponent reduction is FP64.  Geometric means take one more pass that sums ln kappa
@@ -200,10 +201,13 @@ int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N,
  * The interval bounds and widths are staged in one fixed file-scope device array
  * of about 0.5 MiB, which every device that loads the library keeps until the
  * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make this first call before any stream
- * capture.  Every call shares the array and overwrites it: calls that may
- * overlap on the GPU (different streams, or a capture replayed concurrently)
- * race and must be serialised by the caller.  Stream-ordered otherwise.
+ * address (cudaGetSymbolAddress, once per device and safe from several host
+ * threads); make this first call before any stream capture.  The address is not
+ * looked up again, so do not call this entry point after a cudaDeviceReset.
+ * Every call shares the array and overwrites it: calls that may overlap on the
+ * GPU (for example on different streams) race and must be serialised by the
+ * caller.  The host arrays are copied with cudaMemcpyAsync from pageable memory.
+ * Stream-ordered otherwise.
  */
 int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_rows, int64_t N,
                       int32_t K, const int64_t* bounds, int32_t n_steps, const double* widths,

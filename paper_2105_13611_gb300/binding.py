@@ -193,12 +193,30 @@ def make_opts(cut=1e-3, kc_factor=1e-2, precision=PREC_FP32_COMPENSATED):
     return SynthOpts(cut, kc_factor, precision, 0)
 
 
+def _odf_args(kappa, bounds, widths, odf_out, device):
+    """Host arrays of an ODF call after checking the device buffers against them: kappa a
+    float32 [n_rows][N] and odf_out a float64 [n_rows][K][n_steps] CUDA tensor, both on
+    `device` (a mismatch would let the kernel read or write outside the buffers)."""
+    import torch
+    b = _arr(bounds, np.int64)
+    w = _arr(widths, np.float64)
+    if kappa.dtype != torch.float32 or kappa.dim() != 2:
+        raise ValueError(f"kappa must be a float32 [n_rows][N] tensor, got {kappa.dtype} {tuple(kappa.shape)}")
+    if odf_out.dtype != torch.float64:
+        raise ValueError(f"odf_out must be float64, got {odf_out.dtype}")
+    n_rows, N = kappa.shape
+    if tuple(odf_out.shape) != (n_rows, len(b) - 1, len(w)):
+        raise ValueError(f"odf_out has shape {tuple(odf_out.shape)}, expected {(n_rows, len(b) - 1, len(w))}")
+    for name, t in (("kappa", kappa), ("odf_out", odf_out)):
+        if not t.is_cuda or t.device.index != int(device):
+            raise ValueError(f"{name} is on {t.device}, expected cuda:{int(device)}")
+    return b, w, n_rows, N
+
+
 def build_odf_noalloc(device, kappa, bounds, widths, odf_out, mean_kind=MEAN_ARITH, stream=None):
     """build_odf without device allocation (fixed library-owned staging array; see include/mpsa.h)."""
     lib = load_library()
-    b = _arr(bounds, np.int64)
-    w = _arr(widths, np.float64)
-    n_rows, N = kappa.shape
+    b, w, n_rows, N = _odf_args(kappa, bounds, widths, odf_out, device)
     rc = lib.build_odf_noalloc(int(device), _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
                                _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream))
     _check(rc)
@@ -271,9 +289,7 @@ class Context:
                                       _dev(kappa_c_out), _dev(evals_out), C.byref(o), _stream(stream)))
 
     def build_odf(self, kappa, bounds, widths, odf_out, mean_kind=MEAN_ARITH, stream=None):
-        b = _arr(bounds, np.int64)
-        w = _arr(widths, np.float64)
-        n_rows, N = kappa.shape
+        b, w, n_rows, N = _odf_args(kappa, bounds, widths, odf_out, self.device)
         _check(self.lib.build_odf(self.h, _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
                                   _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream)))
 

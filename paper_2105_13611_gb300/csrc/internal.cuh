@@ -26,9 +26,11 @@ int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* 
 // stream capture) (odf.cu).
 int odf_setup();
 
-// Host-side validation of ODF arguments; fills the cumulative widths cw[n_steps+1] (odf.cu).
-int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, const double* widths, int mean_kind,
-              double* cw);
+// Host-side validation of ODF arguments for one launch of n_rows rows (at most 65,535);
+// fills the cumulative widths cw[n_steps+1].  `who` names the entry point in the error
+// message (odf.cu).
+int odf_check(const char* who, int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps,
+              const double* widths, int mean_kind, double* cw);
 
 // Formal solution for D depths on a window grid (spectrum.cu); inputs device-resident.
 int formal_launch(int D, int N, const float* kappa, const float* kc, const float* m, const float* T, double lam0_nm,

@@ -32,6 +32,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -56,6 +57,8 @@ constexpr int kMinSlots = 4;
 constexpr int kCand = ODF_KCAND;                   // candidate buffer (32-bit patterns)
 constexpr long long kMaxInterval = 1ll << 21;      // count < 2^24 and low-bit sums < 2^40 per bin
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxOdfRows = 65535;                // gridDim.y of the ODF launch
+constexpr int kMaxDevices = 64;
 
 struct Target {
     long long k;                 // rank (0-based) of the order statistic
@@ -705,27 +708,30 @@ using namespace mpsa;
 
 namespace mpsa {
 
-int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, const double* widths, int mean_kind,
-              double* cw) {
-    if (n_rows < 1 || N < 1 || K < 1) return fail(MPSA_EINVAL, "build_odf: n_rows %d N %lld K %d", n_rows, (long long)N, K);
-    if (n_steps < 1 || n_steps > kMaxSteps) return fail(MPSA_EINVAL, "build_odf: n_steps = %d (1..%d)", n_steps, kMaxSteps);
+int odf_check(const char* who, int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps,
+              const double* widths, int mean_kind, double* cw) {
+    if (n_rows < 1 || N < 1 || K < 1) return fail(MPSA_EINVAL, "%s: n_rows %d N %lld K %d", who, n_rows, (long long)N, K);
+    // one CTA per (interval, row): the rows are the grid's y dimension
+    if (n_rows > kMaxOdfRows) return fail(MPSA_EINVAL, "%s: n_rows = %d (at most %d per call)", who, n_rows, kMaxOdfRows);
+    if (n_steps < 1 || n_steps > kMaxSteps) return fail(MPSA_EINVAL, "%s: n_steps = %d (1..%d)", who, n_steps, kMaxSteps);
     if (mean_kind != MPSA_MEAN_ARITH && mean_kind != MPSA_MEAN_GEOM)
-        return fail(MPSA_EINVAL, "build_odf: mean_kind %d (0 arithmetic, 1 geometric)", mean_kind);
-    if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "build_odf: bounds outside [0, N]");
+        return fail(MPSA_EINVAL, "%s: mean_kind %d (0 arithmetic, 1 geometric)", who, mean_kind);
+    if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "%s: bounds outside [0, N]", who);
     for (int k = 0; k < K; ++k) {
         const int64_t len = bounds[k + 1] - bounds[k];
-        if (len < 1) return fail(MPSA_EINVAL, "build_odf: bounds not strictly increasing at %d", k);
-        if (len >= kMaxInterval) return fail(MPSA_EINVAL, "build_odf: interval %d has %lld points (max 2^21-1)", k, (long long)len);
+        if (len < 1) return fail(MPSA_EINVAL, "%s: bounds not strictly increasing at %d", who, k);
+        if (len >= kMaxInterval)
+            return fail(MPSA_EINVAL, "%s: interval %d has %lld points (max 2^21-1)", who, k, (long long)len);
     }
     // cumulative widths: FP64 left-to-right partial sums, the last forced to 1
     double acc = 0.0;
     cw[0] = 0.0;
     for (int s = 0; s < n_steps; ++s) {
-        if (!(widths[s] > 0) || !isfinite(widths[s])) return fail(MPSA_EINVAL, "build_odf: widths[%d] = %g", s, widths[s]);
+        if (!(widths[s] > 0) || !isfinite(widths[s])) return fail(MPSA_EINVAL, "%s: widths[%d] = %g", who, s, widths[s]);
         acc = acc + widths[s];
         cw[s + 1] = acc;
     }
-    if (fabs(acc - 1.0) > 1e-12) return fail(MPSA_EINVAL, "build_odf: widths sum to %.17g", acc);
+    if (fabs(acc - 1.0) > 1e-12) return fail(MPSA_EINVAL, "%s: widths sum to %.17g", who, acc);
     cw[n_steps] = 1.0;
     return MPSA_OK;
 }
@@ -733,12 +739,16 @@ int odf_check(int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps, 
 int odf_setup() {
     int dev = 0;
     MPSA_CUDA_TRY(cudaGetDevice(&dev));
-    static unsigned attr_set = 0;   // one bit per device
-    if (!(attr_set & (1u << (dev & 31)))) {
-        MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)odf_smem_bytes(kMaxSteps)));
-        attr_set |= 1u << (dev & 31);
-    }
+    if (dev < 0 || dev >= kMaxDevices) return fail(MPSA_EINVAL, "build_odf: device %d", dev);
+    // once per device (thread-safe): the kernel's dynamic shared-memory limit
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t err[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        err[dev] = cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)odf_smem_bytes(kMaxSteps));
+    });
+    if (err[dev] != cudaSuccess)
+        return fail(MPSA_ECUDA, "build_odf: cudaFuncSetAttribute: %s", cudaGetErrorString(err[dev]));
     return MPSA_OK;
 }
 
@@ -760,7 +770,7 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     if (!ctx || !kappa || !bounds || !widths || !odf_out) return fail(MPSA_EINVAL, "build_odf: NULL argument");
     std::vector<double> cw(n_steps >= 1 && n_steps <= kMaxSteps ? n_steps + 1 : 1);
     int r;
-    if ((r = odf_check(n_rows, N, K, bounds, n_steps, widths, mean_kind, cw.data()))) return r;
+    if ((r = odf_check("build_odf", n_rows, N, K, bounds, n_steps, widths, mean_kind, cw.data()))) return r;
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     Scratch sc(st);
@@ -794,20 +804,24 @@ constexpr size_t kNoAllocBytes =
     (size_t)(kNoAllocMaxIntervals + 1) * sizeof(int64_t) + (size_t)(2 * kMaxSteps + 1) * sizeof(double);
 static __device__ __align__(256) unsigned char g_odf_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the scratch array, per device.  In host code the symbol name is
+// Device address of the scratch array, looked up once per device (std::call_once, so
+// first calls from several host threads are safe).  In host code the symbol name is
 // only a host-side stand-in; the address comes from cudaGetSymbolAddress with the
-// device current.
-static void* g_noalloc_ptr[64];
+// device current.  The address is kept for the life of the process: it does not
+// survive a cudaDeviceReset, after which this entry point must not be called.
+static void* g_noalloc_ptr[kMaxDevices];
+static cudaError_t g_noalloc_err[kMaxDevices];
+static std::once_flag g_noalloc_once[kMaxDevices];
 
 int noalloc_scratch(int device, unsigned char** out) {
-    if (device < 0 || device >= 64) return fail(MPSA_EINVAL, "build_odf_noalloc: device %d", device);
-    if (!g_noalloc_ptr[device]) {
+    if (device < 0 || device >= kMaxDevices) return fail(MPSA_EINVAL, "build_odf_noalloc: device %d", device);
+    std::call_once(g_noalloc_once[device], [&] {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_odf_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(MPSA_ECUDA, "build_odf_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_noalloc_ptr[device] = p;
-    }
+        g_noalloc_err[device] = cudaGetSymbolAddress(&p, g_odf_noalloc_scratch);
+        if (g_noalloc_err[device] == cudaSuccess) g_noalloc_ptr[device] = p;
+    });
+    if (g_noalloc_err[device] != cudaSuccess || !g_noalloc_ptr[device])
+        return fail(MPSA_ECUDA, "build_odf_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(g_noalloc_err[device]));
     *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
     return MPSA_OK;
 }
@@ -819,36 +833,15 @@ extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_r
                                  const int64_t* bounds, int32_t n_steps, const double* widths, int32_t mean_kind,
                                  double* odf_out, void* stream) {
     if (!kappa || !bounds || !widths || !odf_out) return fail(MPSA_EINVAL, "build_odf_noalloc: NULL argument");
+    // the fixed array's limit first: bounds[K] is read by the shared checks below
     if (K > kNoAllocMaxIntervals)
         return fail(MPSA_EINVAL, "build_odf_noalloc: K = %d intervals exceeds the fixed scratch limit of %d", K,
                     kNoAllocMaxIntervals);
-    if (n_rows < 1 || N < 1 || K < 1)
-        return fail(MPSA_EINVAL, "build_odf_noalloc: n_rows %d N %lld K %d", n_rows, (long long)N, K);
-    if (n_steps < 1 || n_steps > kMaxSteps)
-        return fail(MPSA_EINVAL, "build_odf_noalloc: n_steps = %d (1..%d)", n_steps, kMaxSteps);
-    if (mean_kind != MPSA_MEAN_ARITH && mean_kind != MPSA_MEAN_GEOM)
-        return fail(MPSA_EINVAL, "build_odf_noalloc: mean_kind %d (0 arithmetic, 1 geometric)", mean_kind);
-    if (bounds[0] < 0 || bounds[K] > N) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds outside [0, N]");
-    for (int k = 0; k < K; ++k) {
-        const int64_t len = bounds[k + 1] - bounds[k];
-        if (len < 1) return fail(MPSA_EINVAL, "build_odf_noalloc: bounds not strictly increasing at %d", k);
-        if (len >= kMaxInterval)
-            return fail(MPSA_EINVAL, "build_odf_noalloc: interval %d has %lld points (max 2^21-1)", k, (long long)len);
-    }
     double cw[kMaxSteps + 1];
-    double acc = 0.0;
-    cw[0] = 0.0;
-    for (int s = 0; s < n_steps; ++s) {
-        if (!(widths[s] > 0) || !isfinite(widths[s]))
-            return fail(MPSA_EINVAL, "build_odf_noalloc: widths[%d] = %g", s, widths[s]);
-        acc = acc + widths[s];
-        cw[s + 1] = acc;
-    }
-    if (fabs(acc - 1.0) > 1e-12) return fail(MPSA_EINVAL, "build_odf_noalloc: widths sum to %.17g", acc);
-    cw[n_steps] = 1.0;
+    int r;
+    if ((r = odf_check("build_odf_noalloc", n_rows, N, K, bounds, n_steps, widths, mean_kind, cw))) return r;
     MPSA_CUDA_TRY(cudaSetDevice(device));
     unsigned char* base;
-    int r;
     if ((r = noalloc_scratch(device, &base))) return r;
     // layout: bounds [K+1] int64 | cumulative widths [n_steps+1] | widths [n_steps]
     int64_t* d_b = reinterpret_cast<int64_t*>(base);
@@ -858,10 +851,5 @@ extern "C" int build_odf_noalloc(int32_t device, const float* kappa, int32_t n_r
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_b, bounds, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_cw, cw, (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
     MPSA_CUDA_TRY(cudaMemcpyAsync(d_w, widths, n_steps * sizeof(double), cudaMemcpyHostToDevice, st));
-    MPSA_CUDA_TRY(cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)odf_smem_bytes(kMaxSteps)));
-    k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_b, n_steps, d_cw, d_w,
-                                                                         odf_out, mean_kind == MPSA_MEAN_GEOM);
-    MPSA_CUDA_TRY(cudaGetLastError());
-    return MPSA_OK;
+    return odf_launch(kappa, n_rows, N, K, d_b, n_steps, d_cw, d_w, odf_out, mean_kind, st);
 }

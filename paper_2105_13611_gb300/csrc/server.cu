@@ -257,6 +257,7 @@ int mpsa_server_create(mpsa_server** out, mpsa_ctx* ctx, size_t hbm_budget_bytes
     if (!out || !ctx) return fail(MPSA_EINVAL, "mpsa_server_create: NULL argument");
     if (max_inflight < 1 || max_inflight > 64) return fail(MPSA_EINVAL, "mpsa_server_create: max_inflight %d", max_inflight);
     if (rows_per_chunk < 1) rows_per_chunk = 8;
+    if (rows_per_chunk > 65535) rows_per_chunk = 65535;   // rows of one ODF launch
     if (ctx->L < 1 || !ctx->d_pop) return fail(MPSA_ESTATE, "mpsa_server_create: load a line list and a grid first");
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     mpsa_server* s = new mpsa_server();
@@ -327,7 +328,9 @@ int mpsa_server_submit(mpsa_server* s, const mpsa_request* q, int64_t* ticket) {
             }
         if ((rc = check_grid(&q->grid, &r->N))) { delete r; return rc; }
         r->cw.resize(q->n_steps + 1);
-        if ((rc = odf_check(q->n_sel, r->N, q->K, q->bounds, q->n_steps, q->widths, q->mean_kind, r->cw.data()))) {
+        // the ODF runs in launches of at most rows_per_chunk rows
+        if ((rc = odf_check("mpsa_server_submit", std::min(q->n_sel, s->rows_per_chunk), r->N, q->K, q->bounds,
+                            q->n_steps, q->widths, q->mean_kind, r->cw.data()))) {
             delete r;
             return rc;
         }

@@ -1456,7 +1456,9 @@ int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int au
         if (q.K > 0) {
             if (!q.bounds || !q.widths || !q.odf_out) return fail(MPSA_EINVAL, "mpsa_batch_create: group %d ODF args", g);
             std::vector<double> cw(q.n_steps >= 1 && q.n_steps <= 32 ? q.n_steps + 1 : 1);
-            if ((r = odf_check(q.n_sel, G.N, q.K, q.bounds, q.n_steps, q.widths, q.mean_kind, cw.data()))) return r;
+            if ((r = odf_check("mpsa_batch_create", q.n_sel, G.N, q.K, q.bounds, q.n_steps, q.widths, q.mean_kind,
+                               cw.data())))
+                return r;
             G.K = q.K;
             G.n_steps = q.n_steps;
             G.mean_kind = q.mean_kind;

@@ -79,39 +79,9 @@ int voigt_host_consts64(VoigtConsts64* out) {
 }
 
 int voigt_host_consts(VoigtConsts* out) {
-    const int n = 2 * kGHPairs;
     double nodes[kGHPairs], weights[kGHPairs];
-    int found = 0;
-    // The positive roots of H_n lie in (0, sqrt(2n+1)); bracket sign changes on a
-    // fine scan, then bisect to full precision.
-    const double xmax = sqrt(2.0 * n + 1.0) + 1.0;
-    const int steps = 20000;
-    double xprev = 1e-9, hprev, dummy;
-    hermite(n, xprev, &hprev, &dummy);
-    for (int i = 1; i <= steps && found < kGHPairs; ++i) {
-        double x = xmax * i / steps, h;
-        hermite(n, x, &h, &dummy);
-        if ((h > 0) != (hprev > 0)) {
-            double lo = xprev, hi = x, hlo = hprev;
-            for (int it = 0; it < 200; ++it) {
-                double mid = 0.5 * (lo + hi), hm;
-                hermite(n, mid, &hm, &dummy);
-                if ((hm > 0) == (hlo > 0)) { lo = mid; hlo = hm; } else { hi = mid; }
-            }
-            nodes[found++] = 0.5 * (lo + hi);
-        }
-        xprev = x;
-        hprev = h;
-    }
-    if (found != kGHPairs) return fail(MPSA_EINVAL, "voigt_init: found %d Hermite roots", found);
-    // omega_k = 2^{n-1} n! sqrt(pi) / (n^2 H_{n-1}(x_k)^2)
-    double fact = 1.0;
-    for (int k = 2; k <= n; ++k) fact *= k;
-    for (int k = 0; k < kGHPairs; ++k) {
-        double hn, hn1;
-        hermite(n, nodes[k], &hn, &hn1);
-        weights[k] = pow(2.0, n - 1) * fact * sqrt(kPI) / ((double)n * n * hn1 * hn1);
-    }
+    int r = gauss_hermite(2 * kGHPairs, nodes, weights);
+    if (r != MPSA_OK) return r;
     VoigtConsts& h = *out;
     const double dl = (double)kGHDelta;
     const double pre = exp(dl * dl) / kPI;

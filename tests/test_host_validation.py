@@ -50,6 +50,7 @@ def test_noalloc_rejects_invalid_arguments(lib):
         (N, [-1, 400, 1000], W12, 0, 1),            # negative start
         (1 << 23, [0, 1 << 21], W12, 0, 1),         # interval of 2^21 points
         (N, np.arange(65538), W12, 0, 1),           # more than 65,536 intervals
+        (N, good_b, W12, 0, 65536),                 # more rows than one launch's grid holds
     ]
     for N_, b, w, mk, rows in cases:
         assert call_noalloc(lib, N_, b, w, mk, rows) == -1, (N_, len(b), len(w), mk, rows)
@@ -60,3 +61,23 @@ def test_grid_size_matches_the_oracle(lib):
     for lam0, lam1, R in [(300.0, 400.0, 2e6), (9.0, 10000.0, 2e6), (300.0, 300.0001, 5e5), (500.0, 1500.0, 1000.0)]:
         g = binding.LGrid(lam0, lam1, R)
         assert lib.mpsa_grid_size(C.byref(g)) == sy.grid_size(lam0, lam1, R)
+
+
+def test_binding_checks_odf_buffers_before_the_call(lib):
+    # dtype, shape and device of the ODF buffers are checked in the binding before any C call
+    # (a float32 or undersized output would otherwise be written past its end)
+    import torch
+    from paper_2105_13611_gb300 import binding
+    b, w = np.array([0, 400, 1000]), W12
+    k32 = torch.zeros((2, 1000), dtype=torch.float32)
+    good = torch.zeros((2, 2, 12), dtype=torch.float64)
+    bad = [
+        (torch.zeros((2, 1000), dtype=torch.float64), good, "float32"),      # kappa not float32
+        (k32, torch.zeros((2, 2, 12), dtype=torch.float32), "float64"),     # output not float64
+        (k32, torch.zeros((2, 2, 11), dtype=torch.float64), "shape"),       # output too small
+        (k32, torch.zeros((1, 2, 12), dtype=torch.float64), "shape"),       # rows differ
+        (k32, good, "cuda:0"),                                              # host tensors
+    ]
+    for kappa, out, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            binding.build_odf_noalloc(0, kappa, b, w, out)

@@ -53,3 +53,18 @@ def test_two_ranks_disjoint_rows_and_reductions():
 def test_single_process_identity():
     assert reduce_scalar(3.0, "max") == 3.0
     assert np.array_equal(rows_for_rank(5, 0, 1), np.arange(5))
+
+
+def test_bench_rows_per_rank_are_disjoint_and_same_mix():
+    # bench.py's rows under torchrun come from rows_for_rank: disjoint across ranks, rank 0
+    # keeps the single-GPU rows, and every rank takes one row of each cost class (a
+    # temperature neighbour of the same pressure)
+    import bench
+    for world in (1, 2, 4, 8):
+        per = [bench.batch_points(r, 8, world) for r in range(world)]
+        flat = np.concatenate(per)
+        assert len(set(flat.tolist())) == len(flat) and np.all((flat >= 0) & (flat < 1425))
+        assert np.array_equal(per[0], bench.TABLE_ROWS)
+        for rows in per:
+            assert np.array_equal(rows % 25, np.array(bench.TABLE_ROWS) % 25)
+            assert np.all(np.abs(rows // 25 - np.array(bench.TABLE_ROWS) // 25) < world)
