@@ -82,3 +82,37 @@ def spectrum(lines, species_el, species_stage, el, m, T, P, win_grid, mus, cut=1
         for q, mu in enumerate(mus):
             out[q, j] = formal_solution(tau, S[:, j], mu)
     return out
+
+
+def spectrum_at(lines, species_el, species_stage, el, m, T, P, win_grid, mus, js, cut=1e-3, kc_factor=1e-2,
+                abund_scale=None, vturb=0.0, slack_band=3e-5):
+    """I[n_mu][len(js)] of one atmosphere at the window grid indices js only (same steps as
+    `spectrum`; the opacity of each depth comes from synthesis.kappa_at), together with a bound
+    on how far I can move when contributions inside the edge-slack band of the cut are taken
+    or dropped: dI[n_mu][len(js)] = max over the two one-sided perturbations kappa +- slack of
+    |I(kappa +- slack) - I(kappa)|."""
+    js = np.asarray(js, dtype=np.int64)
+    D = len(m)
+    kap = np.empty((D, len(js)))
+    sl = np.empty((D, len(js)))
+    S = np.empty((D, len(js)))
+    lam_cm = synthesis.grid_lambda_nm(win_grid.lam0_nm, win_grid.R, js) * 1e-7
+    for d in range(D):
+        pl = synthesis.prepare(lines, species_el, species_stage, el, T[d], P[d], win_grid, cut, kc_factor,
+                               abund_scale, vturb)
+        k, s = synthesis.kappa_at(pl, js, slack_band)
+        kap[d] = k + pl.kappa_c
+        sl[d] = s
+        S[d] = planck_lambda(lam_cm, T[d])
+    out = np.empty((len(mus), len(js)))
+    dI = np.zeros((len(mus), len(js)))
+    for n in range(len(js)):
+        tau = optical_depth(kap[:, n], m)
+        tau_hi = optical_depth(kap[:, n] + sl[:, n], m)
+        tau_lo = optical_depth(np.maximum(kap[:, n] - sl[:, n], 0.0), m)
+        for q, mu in enumerate(mus):
+            out[q, n] = formal_solution(tau, S[:, n], mu)
+            if np.any(sl[:, n] > 0):
+                dI[q, n] = max(abs(formal_solution(tau_hi, S[:, n], mu) - out[q, n]),
+                               abs(formal_solution(tau_lo, S[:, n], mu) - out[q, n]))
+    return out, dI

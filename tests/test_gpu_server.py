@@ -4,7 +4,9 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from oracle import odf as od
 from oracle import spectrum as spc
+from oracle import synthesis as sy
 
 from gpu_util import ODF_RTOL, gpu_context
 
@@ -98,3 +100,49 @@ def test_budget_admission_and_errors():
     assert all(np.array_equal(r, res[0]) for r in res)
     assert srv.stats()["bytes_peak"] <= 64 << 20
     srv.close()
+
+
+def test_served_results_match_the_oracle():
+    # every request served in the mix against the FP64 oracle: spectra within 1e-4 (plus the
+    # edge-slack bound), arithmetic ODFs end to end (oracle opacity -> oracle ODF; order
+    # statistics inherit the opacity bound 1e-4 (o + kappa_c) + slack), geometric ODFs against
+    # the oracle's geometric ODF of the same rows' GPU opacity (<= 1e-5) and the served
+    # continuum against the oracle's
+    import torch
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_tiny(n_lines=80, lam=(299.9, 300.6), R=5e5, seed=31)
+    ctx, L = gpu_context(w)
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    reqs = make_requests(w)
+    srv = binding.Server(ctx, hbm_budget_bytes=8 << 30, max_inflight=4, rows_per_chunk=4)
+    tickets = [srv.submit_spectrum(*a[:3], a[3], MUS) if kind == "spec" else srv.submit_odf(*a) for kind, a in reqs]
+    served = [srv.wait(t)[0] for t in tickets]
+    srv.close()
+    for (kind, a), res in zip(reqs, served):
+        if kind == "spec":
+            m, T, P, win = a
+            N = res.shape[1]
+            js = np.arange(N)
+            o, dI = spc.spectrum_at(L, se, ss, el, m, T, P, win, MUS, js)
+            assert np.all(np.abs(res.astype(np.float64) - o) <= 1e-4 * o + dI * 1.001)
+            continue
+        odf_g, kc_g = res
+        sel, g, b, wd = a[:4]
+        geom = len(a) > 4 and a[4] == binding.MEAN_GEOM
+        if geom:
+            N = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
+            k = torch.empty((len(sel), N), dtype=torch.float32, device="cuda")
+            ctx.synth_opacity(g, sel, k)
+            torch.cuda.synchronize()
+            kn = k.cpu().numpy().astype(np.float64)
+        for r, p in enumerate(sel):
+            pl = sy.prepare(L, se, ss, el, w.T[p], w.P[p], g, w.cut, w.kc_factor)
+            assert abs(float(kc_g[r]) / pl.kappa_c - 1) < 1e-5
+            if geom:
+                o = od.odf(kn[r], b, wd, mean="geom")
+                assert np.all(np.abs(odf_g[r] - o) <= ODF_RTOL * np.abs(o) + 1e-300)
+            else:
+                k_o, slack, _ = sy.kappa_dense(pl)
+                o = od.odf(k_o, b, wd)
+                assert np.all(np.abs(odf_g[r] - o) <= 1e-4 * (o + pl.kappa_c) + slack.max() * 1.001)

@@ -136,15 +136,16 @@ def test_full_size_sampled():
 
 
 def test_precision_variants_against_oracle():
-    # the three library precisions on the same rows: all within the opacity tolerance; the
-    # all-FP64 variant within 1e-9 (outside the edge slack), compensated FP32 no worse than naive
+    # the four library precisions on the same rows (compensated FP32, plain FP32 sums, all FP64,
+    # compensated FP32 from an FP32-rounded population table): all within the opacity tolerance;
+    # the all-FP64 variant within 1e-7 (outside the edge slack, the FP32 output rounding)
     w = wl.config_tiny(n_lines=400, lam=(300.0, 303.1), seed=8)
     ctx, L = gpu_context(w)
     sel = np.arange(4)
-    res = {p: gpu_synth(ctx, w, sel, precision=p)[0] for p in (0, 1, 2)}
+    res = {p: gpu_synth(ctx, w, sel, precision=p)[0] for p in (0, 1, 2, 3)}
     for s in sel:
         pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
-        for p in (0, 1, 2):
+        for p in (0, 1, 2, 3):
             bad, _, _ = opacity_violations(res[p][s], k, pl.kappa_c, slack)
             assert len(bad) == 0, (p, s)
         m = slack == 0
@@ -152,12 +153,26 @@ def test_precision_variants_against_oracle():
         assert rel64.max() < 1e-7        # FP32 output rounding bounds it
 
 
+def _table_row_oracle(job):
+    # one bench row at sampled grid points, in a spawned process (own copy of the line list)
+    r, T, P, js = job
+    w = wl.config_table()
+    L = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    pl = sy.prepare(L, se, ss, el, T, P, w.grid, w.cut, w.kc_factor)
+    ko, so = sy.kappa_at(pl, js)
+    return r, pl.kappa_c, ko, so
+
+
 def test_table_workload_sampled():
     # the benchmark's own workload and launch: 5e6 lines over 9-10000 nm at R = 2e6 (14.0 M
     # points), the 8 (T, P) rows of one bench step in one synth_opacity call, then build_odf
-    # over the 328 intervals.  The oracle evaluates sampled points of two rows one by one
-    # (random points and the cores of the strongest lines) and the ODF of sampled intervals on
-    # the same FP32 opacity.
+    # over the 328 intervals.  The oracle evaluates 60 sampled points of every row one by one
+    # (random points and points at and beside the cores of the strongest lines of the row, in
+    # spawned processes) and the ODF of sampled intervals on the same FP32 opacity.
+    import multiprocessing as mp
+
     import torch
     from oracle import odf as od
     from paper_2105_13611_gb300 import binding
@@ -176,17 +191,23 @@ def test_table_workload_sampled():
     se, ss = wl.species_table(w.n_metals)
     rng = np.random.default_rng(5)
     lnq = np.log1p(1 / w.grid.R)
-    for i in (5, 0):   # row 1044 (strong damping, far wings) and row 277
-        r = rows[i]
-        pl = sy.prepare(L, se, ss, el, w.T[r], w.P[r], w.grid, w.cut, w.kc_factor)
-        assert abs(float(kc[i]) / pl.kappa_c - 1) < 1e-5
-        strong = np.argsort(pl.kappa0)[-2:]
-        centres = np.round(np.log(L.lam_nm[strong] / w.grid.lam0_nm) / lnq).astype(np.int64)
-        js = np.unique(np.clip(np.r_[rng.integers(0, N, 4), centres, centres + 5], 0, N - 1))
-        kg = kap[i, torch.from_numpy(js).cuda()].cpu().numpy()
-        ko, so = sy.kappa_at(pl, js)
-        bad, err, bound = opacity_violations(kg, ko, pl.kappa_c, so)
-        assert len(bad) == 0, (r, js[bad[:5]], rel_report(kg, ko, pl.kappa_c))
+    # the strongest lines of the list by gf e^{-E/kT} at each row's temperature
+    strength = L.log_gf.astype(np.float64)
+    jobs, samples = [], {}
+    for i, r in enumerate(rows):
+        top = np.argsort(strength - L.E_eV / (8.617333262e-5 * w.T[r]) / np.log(10))[-6:]
+        centres = np.round(np.log(L.lam_nm[top] / w.grid.lam0_nm) / lnq).astype(np.int64)
+        js = np.unique(np.clip(np.r_[rng.integers(0, N, 42), centres, centres + 4, centres - 9], 0, N - 1))
+        samples[r] = (i, js, kap[i, torch.from_numpy(js).cuda()].cpu().numpy())
+        jobs.append((r, float(w.T[r]), float(w.P[r]), js))
+    with mp.get_context("spawn").Pool(min(len(rows), 8)) as pool:
+        res = pool.map(_table_row_oracle, jobs)
+    for r, kc_o, ko, so in res:
+        i, js, kg = samples[r]
+        assert len(js) >= 50
+        assert abs(float(kc[i]) / kc_o - 1) < 1e-5, r
+        bad, err, bound = opacity_violations(kg, ko, kc_o, so)
+        assert len(bad) == 0, (r, js[bad[:5]], rel_report(kg, ko, kc_o))
         og = odf[i].cpu().numpy()
         for k in rng.choice(w.n_intervals, 4, replace=False):
             x = kap[i, int(b[k]):int(b[k + 1])].cpu().numpy().astype(np.float64)

@@ -64,3 +64,18 @@ def test_spectrum_isothermal_is_planck():
     B = spc.planck_lambda(sy.grid_lambda_nm(w.grid.lam0_nm, w.grid.R, np.arange(N)) * 1e-7, 7000.0)
     assert I.shape == (len(MUS), N)
     assert np.allclose(I, B[None, :], rtol=1e-12)
+
+
+def test_sampled_spectrum_equals_dense():
+    # spectrum_at evaluates the same steps at selected grid points only (kappa_at per depth);
+    # it must reproduce the dense spectrum there, and its slack bound is non-negative
+    import workloads as wl
+    w = wl.config_tiny(n_lines=25, lam=(299.98, 300.06), R=5e5, seed=4)
+    L = w.lines(); el = wl.elements(w.n_metals); se, ss = wl.species_table(w.n_metals)
+    m, T, P = spc.grey_atmosphere(9, 6500.0, 4.0)
+    win = wl.Grid(300.0, 300.04, 5e5)
+    dense = spc.spectrum(L, se, ss, el, m, T, P, win, MUS)
+    js = np.array([0, 3, 17, 40, dense.shape[1] - 1])
+    at, dI = spc.spectrum_at(L, se, ss, el, m, T, P, win, MUS, js)
+    assert np.allclose(at, dense[:, js], rtol=1e-13, atol=0)
+    assert np.all(dI >= 0)
