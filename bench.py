@@ -56,7 +56,7 @@ def parse():
                    help="comma-separated table rows (T index * 25 + P index) instead of the default batch")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
-    p.add_argument("--mode", choices=["step", "serve", "batch", "precision", "bins"], default="step",
+    p.add_argument("--mode", choices=["step", "serve", "batch", "precision", "bins", "table"], default="step",
                    help="step: the throughput benchmark; serve: Poisson request stream through the server; "
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
@@ -760,6 +760,69 @@ def precision_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def table_arm(args):
+    """The whole ODF table once: every (T, P) row of the 57 x 25 grid through synth_opacity and
+    build_odf, in chunks of 16 rows, timed with CUDA events per chunk (inputs resident: the
+    line list and the population table).  Prints the wall time, the line-evaluation rate and
+    the ODF (T, P) points per second of the whole table, and the slowest chunks."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    ctx = binding.Context(0)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    K = w.n_intervals
+    bounds = wl.equal_intervals(N, K)
+    chunk = 16
+    rows = np.arange(len(w.T), dtype=np.int32)
+    kap = torch.empty((chunk, N), dtype=torch.float32, device="cuda")
+    kc = torch.empty(chunk, dtype=torch.float32, device="cuda")
+    ev = torch.empty(chunk, dtype=torch.int64, device="cuda")
+    odf = torch.empty((len(rows), K, len(w.widths)), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    opts = binding.make_opts(w.cut, w.kc_factor)
+    # warm-up on the first chunk
+    ctx.synth_opacity(w.grid, rows[:chunk], kap, kc, ev, opts=opts, stream=st)
+    ctx.build_odf(kap, bounds, w.widths, odf[:chunk], stream=st)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ctx.profile_enable(True)
+    ctx.profile_read(binding.KERNEL_PROFILE)
+    ctx.profile_read(binding.KERNEL_ODF)
+    evs, per_chunk = 0, []
+    t0 = time.perf_counter()
+    for i in range(0, len(rows), chunk):
+        sel = rows[i:i + chunk]
+        n = len(sel)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx.synth_opacity(w.grid, sel, kap[:n], kc[:n], ev[:n], opts=opts, stream=st)
+        ctx.build_odf(kap[:n], bounds, w.widths, odf[i:i + n], stream=st)
+        e1.record(st)
+        e1.synchronize()
+        per_chunk.append((int(sel[0]), int(sel[-1]), e0.elapsed_time(e1) / 1e3, int(ev[:n].sum())))
+        evs += per_chunk[-1][3]
+    wall = time.perf_counter() - t0
+    tiles_ms, _ = ctx.profile_read(binding.KERNEL_PROFILE)
+    odf_ms, _ = ctx.profile_read(binding.KERNEL_ODF)
+    clk = clocks.stop()
+    gpu_s = sum(c[2] for c in per_chunk)
+    slow = sorted(per_chunk, key=lambda c: -c[2])[:5]
+    out = {"mode": "table", "metric": "whole 57 x 25 ODF table: wall time, line-evals/s, ODF (T,P) points/s",
+           "rows": len(rows), "grid_points": N, "intervals": K, "lines": len(lines), "chunk_rows": chunk,
+           "wall_s": wall, "gpu_s": gpu_s, "evals": evs, "evals_per_s": evs / gpu_s,
+           "odf_points_per_s": len(rows) / gpu_s, "k_tiles_s": tiles_ms / 1e3, "k_odf_s": odf_ms / 1e3,
+           "slowest_chunks": [{"rows": [a, b], "s": t, "evals": e} for a, b, t, e in slow],
+           "clocks": clk, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
 def measured_traffic(kernel, sources, rows):
     """DRAM bytes (read + written) per launch of `kernel` from the ncu summary in
     profiles/traffic_table_workload.md, or None when that capture was taken on other rows
@@ -794,6 +857,9 @@ def main():
         return
     if args.mode == "bins":
         bins_arm(args)
+        return
+    if args.mode == "table":
+        table_arm(args)
         return
     if args.mode == "serve":
         serve_arm(args)

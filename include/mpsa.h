@@ -19,6 +19,10 @@
  *  - A context (mpsa_ctx) owns the resident device data (line list, element
  *    and species tables, FP64 population table).  A context is bound to one
  *    device and must not be used from two host threads at once.
+ *  - Per-call scratch is stream-ordered device memory from a memory pool owned by
+ *    the context (cudaMallocFromPoolAsync / cudaFreeAsync on the call's stream).
+ *    The pool keeps freed memory cached for the next call until mpsa_destroy, so
+ *    the device memory a context holds grows to the largest scratch of its calls.
  */
 #ifndef MPSA_H
 #define MPSA_H
@@ -51,7 +55,8 @@ const char* mpsa_version(void);
 /* Element table (host arrays of length n_elements).  Element 0 must be hydrogen
  * (its neutral stage supplies the van der Waals perturbers n_HI).  Each element
  * ionises once (stages I and II) with fixed partition functions U1, U2 and
- * first ionisation energy chi_eV; log_eps is the abundance (H = 12). */
+ * first ionisation energy chi_eV; log_eps is the abundance (H = 12).  The
+ * multi-stage table is mpsa_eos (set_atmosphere_grid_eos). */
 typedef struct {
     int32_t n_elements;
     const double* mass_amu;
@@ -90,6 +95,11 @@ typedef struct {
     double kc_factor;   /* flat continuum kappa_c = kc_factor * median kappa0 (default 1e-2) */
     int32_t precision;  /* MPSA_PREC_* (default compensated FP32)                           */
     int32_t tile;       /* grid points per CTA tile; 0 = library default                   */
+    int32_t continuum;  /* synth_spectrum: 0 = the flat continuum of the cut rule (default);
+                           an OR of MPSA_CONT_* = that closed-form continuum (synth_continuum)
+                           per depth and wavelength in the radiative transfer instead (the
+                           cut rule keeps the flat continuum)                                */
+    int32_t reserved;   /* 0 */
 } mpsa_synth_opts;
 
 #define MPSA_PREC_FP32_COMPENSATED 0   /* FP32 profiles, chunked FP32 partials + Kahan fold */
@@ -105,7 +115,8 @@ typedef struct {
  * the quantities of Eq. (l_nu_line).
  *   n_species, species_element[n_species], species_stage[n_species] (host):
  *     species s belongs to element species_element[s] (index into the element
- *     table of set_atmosphere_grid) in stage species_stage[s] (0 = I, 1 = II).
+ *     table of set_atmosphere_grid) in stage species_stage[s] (0 = I, 1 = II, ...,
+ *     4 = V; stages above II need set_atmosphere_grid_eos).
  *   lines (host): the list, ascending in lambda_nm (MPSA_EINVAL otherwise).
  * Replaces any previously loaded list.  Synchronises the device on return.
  * Errors: MPSA_EINVAL (n_lines < 1, non-finite or unsorted lambda, species out
@@ -116,7 +127,9 @@ int load_linelist(mpsa_ctx* ctx, int32_t n_species, const int32_t* species_eleme
 
 /*
  * set_atmosphere_grid -- build the FP64 population table (paper Sect. 2.1 and
- * App. A: Saha-Boltzmann populations with n_e from charge conservation).
+ * App. A: Saha-Boltzmann populations with n_e from charge conservation), for
+ * elements with stages I and II and constant partition functions (the two-stage
+ * case of set_atmosphere_grid_eos, which solves it).
  *   el (host): element table.
  *   n_points, T[n_points], P[n_points] (host): temperatures [K] and gas
  *     pressures [dyn cm^-2] of the atmosphere points (any set, e.g. a T-P grid).
@@ -124,13 +137,51 @@ int load_linelist(mpsa_ctx* ctx, int32_t n_species, const int32_t* species_eleme
  *     n_comp = 1): per-element abundance multipliers of each composition.
  *   vturb_cm_s: micro-turbulent velocity added to the thermal Doppler width.
  * The table holds, per (composition, point) in that order (row cp = comp *
- * n_points + point): n_e, n_HI, rho and N/U of both stages of every element.
- * Computed on the device in FP64 (one bisection per row).  Synchronises.
+ * n_points + point): n_e, n_HI, rho and N/U of the stages of every element
+ * (layout: mpsa_get_populations).  Computed on the device in FP64.  Synchronises.
  * Errors: MPSA_EINVAL (non-positive T or P, n_elements < 1, bad scales).
  */
 int set_atmosphere_grid(mpsa_ctx* ctx, const mpsa_elements* el, int32_t n_points,
                         const double* T, const double* P, int32_t n_comp,
                         const double* abund_scale, double vturb_cm_s);
+
+/* Element table of the multi-stage equation of state (host arrays).  Element e has stages
+ * 0 .. n_stages[e]-1 (I, II, ..., at most MPSA_MAX_STAGES); chi_eV[e][j] (row-major
+ * [n_elements][MPSA_MAX_STAGES - 1]) is the ionisation energy from stage j to j + 1; the
+ * partition function of stage j is ln U_j(T) = c0 + c1 x + c2 x^2 with x = ln(T / 5040 K) and
+ * (c0, c1, c2) = lnU[e][j][0..2] (row-major [n_elements][MPSA_MAX_STAGES][3]); entries beyond
+ * an element's stages are ignored.  Element 0 must be hydrogen. */
+#define MPSA_MAX_STAGES 5
+typedef struct {
+    int32_t n_elements;
+    const double* mass_amu;
+    const double* log_eps;
+    const int32_t* n_stages;
+    const double* chi_eV;
+    const double* lnU;
+} mpsa_eos;
+
+/*
+ * set_atmosphere_grid_eos -- the population table from the multi-stage equation of state of
+ * paper App. A (without molecules): Saha-Boltzmann ratios between all stages of every element
+ * (up to stage V, App. E) with temperature-dependent partition functions, particle and charge
+ * conservation solved for n_e by Newton-Raphson steps in ln n_e (kept inside a bracket) to a
+ * relative change below 1e-14, in FP64 on the device.  The other arguments, the table and the
+ * errors are those of set_atmosphere_grid (MPSA_EINVAL also for a stage count outside 1..5 or
+ * a non-finite coefficient).  Species of load_linelist may then be in stages 0..4; a species
+ * whose stage its element does not have gives MPSA_EINVAL at synthesis.  Synchronises.
+ */
+int set_atmosphere_grid_eos(mpsa_ctx* ctx, const mpsa_eos* eos, int32_t n_points, const double* T,
+                            const double* P, int32_t n_comp, const double* abund_scale, double vturb_cm_s);
+
+/*
+ * mpsa_get_populations -- copy rows row0 .. row0+n_rows-1 of the population table to the host
+ * (synchronous).  Row layout (*stride doubles per row, 5 + 5 n_elements): T, P, n_e, n_HI, rho,
+ * then N/U of stages I..V of every element (0 for stages the element does not have); the
+ * number densities are in cm^-3, rho in g cm^-3.  stride may be NULL; n_rows = 0 only returns
+ * the stride.  Errors: MPSA_EINVAL, MPSA_ESTATE (no grid), MPSA_ECUDA.
+ */
+int mpsa_get_populations(mpsa_ctx* ctx, int32_t row0, int32_t n_rows, double* out, int32_t* stride);
 
 /* Number of grid points N of a log-lambda grid (0 on invalid input). */
 int64_t mpsa_grid_size(const mpsa_lgrid* grid);
@@ -148,14 +199,40 @@ int64_t mpsa_grid_size(const mpsa_lgrid* grid);
  * A line contributes at grid point j iff its absorption coefficient there is
  * >= cut * kappa_c (FP32 decision).  Profiles are evaluated in FP32 (Voigt,
  * three-tier rational method), populations come from the FP64 table.
- * Stream-ordered, no host synchronisation; scratch is stream-ordered device
- * memory (cudaMallocAsync / cudaFreeAsync), released in stream order after the
- * call's kernels.
+ * Stream-ordered, no host synchronisation; scratch comes from the context's
+ * pool, released in stream order after the call's kernels.
  * Errors: MPSA_ESTATE (no line list / grid), MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
  */
 int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const int32_t* sel,
                   float* kappa_out, float* kappa_c_out, int64_t* evals_out,
                   const mpsa_synth_opts* opts, void* stream);
+
+/*
+ * synth_continuum -- continuous opacity from the closed-form sources of the paper's continuum
+ * (Sect. 2.1: electron scattering, bound-free and free-free absorption of H I, Rayleigh
+ * scattering on H I; App. G groups 'Elec', 'H1', 'Hray'):
+ *   MPSA_CONT_ELEC  n_e sigma_T;
+ *   MPSA_CONT_HBF   H I levels n = 1..8, Kramers' cross-section K_bf / (n^5 nu^3) with Gaunt
+ *                   factor 1 above each edge chi_H / (h n^2), Boltzmann level populations
+ *                   n_HI (2 n^2 / U_HI) e^{-chi_H (1 - 1/n^2)/kT}, times 1 - e^{-h nu/kT};
+ *   MPSA_CONT_HFF   hydrogen free-free, K_ff n_e n_HII / (sqrt(T) nu^3) (1 - e^{-h nu/kT}), Gaunt 1;
+ *   MPSA_CONT_HRAY  n_HI (5.799e-13 / L^4 + 1.422e-6 / L^6 + 2.784 / L^8) cm^2 (L in Angstrom,
+ *                   held at 1300 Angstrom below);
+ * all divided by rho.  The other continuum sources of the paper (H-, He, metals, molecules)
+ * need tabulated cross-sections and are not provided.
+ *   grid (host), n_sel, sel[n_sel] (host): as for synth_opacity (n_sel 1..65535).
+ *   sources: an OR of MPSA_CONT_* (MPSA_CONT_ALL for all four).
+ *   kappa_out (device, float[n_sel][N]): kappa_c [cm^2 g^-1] per row and grid point.
+ * Row constants in FP64, per-point sums in FP32.  Stream-ordered.
+ * Errors: MPSA_ESTATE (no atmosphere grid), MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
+ */
+#define MPSA_CONT_ELEC 1
+#define MPSA_CONT_HBF  2
+#define MPSA_CONT_HFF  4
+#define MPSA_CONT_HRAY 8
+#define MPSA_CONT_ALL  15
+int synth_continuum(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const int32_t* sel, int32_t sources,
+                    float* kappa_out, void* stream);
 
 #define MPSA_MEAN_ARITH 0
 #define MPSA_MEAN_GEOM  1
@@ -228,7 +305,8 @@ typedef struct {
  * wavelength window (paper Eq. Ilambda with LTE source S = B_lambda(T)).
  * For every depth the populations, the line opacity on the window grid (same
  * cut rule as synth_opacity, lines centred outside the window contribute their
- * wings) and the flat continuum are built; tau follows by the trapezoid rule in
+ * wings) and the continuum (the flat one, or opts->continuum's sources of
+ * synth_continuum at every wavelength) are built; tau follows by the trapezoid rule in
  * column mass and I by a linear-source integration from a diffusion lower
  * boundary (I = S + mu dS/dtau) to the surface.
  *   atm (host), win (host): the atmosphere and the window grid (N_win points).
@@ -397,13 +475,15 @@ void mpsa_server_destroy(mpsa_server* s);
  * the library records a CUDA event pair on the launching stream around each
  * launch of its dominant kernels: MPSA_KERNEL_PROFILE (the profile kernel
  * of synth_opacity / synth_spectrum), MPSA_KERNEL_ODF (the kernel of
- * build_odf) and MPSA_KERNEL_BINS (the kernel of odf_intensity).  mpsa_profile_read waits for the recorded events, returns the
+ * build_odf), MPSA_KERNEL_BINS (the kernel of odf_intensity) and
+ * MPSA_KERNEL_CONTINUUM (the kernels of synth_continuum).  mpsa_profile_read waits for the recorded events, returns the
  * summed device time [ms] and launch count of one kernel, and clears its list.
  * Do not enable while capturing a CUDA graph.
  */
-#define MPSA_KERNEL_PROFILE 0
-#define MPSA_KERNEL_ODF     1
-#define MPSA_KERNEL_BINS    2
+#define MPSA_KERNEL_PROFILE   0
+#define MPSA_KERNEL_ODF       1
+#define MPSA_KERNEL_BINS      2
+#define MPSA_KERNEL_CONTINUUM 3
 int mpsa_profile_enable(mpsa_ctx* ctx, int enable);
 int mpsa_profile_read(mpsa_ctx* ctx, int kernel, double* total_ms, int64_t* launches);
 

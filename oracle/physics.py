@@ -90,6 +90,97 @@ def populations(T: float, P: float, el, abund_scale=None) -> Populations:
     return Populations(T, P, n_e, n_nuc, float(n1[0]), rho, stage, NU)
 
 
+def partition_functions(eos, T):
+    """U[e, j](T) = exp(c0 + c1 x + c2 x^2), x = ln(T / 5040 K), for the stages of each element
+    (zero beyond an element's last stage)."""
+    x = math.log(T / 5040.0)
+    c = np.asarray(eos.lnU, dtype=np.float64)
+    U = np.exp(c[:, :, 0] + c[:, :, 1] * x + c[:, :, 2] * x * x)
+    j = np.arange(c.shape[1])[None, :]
+    return np.where(j < np.asarray(eos.n_stages)[:, None], U, 0.0)
+
+
+def populations_eos(T: float, P: float, eos, abund_scale=None, tol: float = 1e-13, max_iter: int = 500) -> Populations:
+    """Multi-stage LTE equation of state (App. A, following the scheme the paper describes).
+
+    Every element e has stages j = 0 .. J_e - 1 linked by the Saha-Boltzmann equation
+    n_{e,j+1} n_e / n_{e,j} = Phi_{e,j}(T) = (2 U_{j+1}/U_j) (2 pi m_e k T/h^2)^{3/2} e^{-chi_j/kT}
+    with temperature-dependent partition functions U_j(T).  Written in the unknowns of App. A,
+    the neutral densities n_{e,0} and the electron density n_e, the equations are
+      f_e   = sum_j n_{e,j} - a_e n_nuc = 0           (nuclei of each element, a_e its fraction)
+      f_ele = sum_e sum_j j n_{e,j} - n_e = 0         (charge conservation)
+    with n_{e,j} = n_{e,0} prod_{i<j} Phi_{e,i}/n_e and n_nuc = P/kT - n_e (particle
+    conservation, no molecules).  They are solved by Newton-Raphson: the Jacobian
+    M = d f / d n is factorised by triangular (LU) decomposition, M dn = -f, and the step is
+    applied until every relative change |dn_i / n_i| is below `tol`.  (The paper stops at
+    1e-4; the oracle iterates to double precision.)  Steps are shortened so that no density
+    drops below a tenth of its value in one iteration.
+    """
+    from scipy.linalg import lu_factor, lu_solve
+    eps = 10.0 ** (np.asarray(eos.log_eps, dtype=np.float64) - 12.0)
+    if abund_scale is not None:
+        eps = eps * np.asarray(abund_scale, dtype=np.float64)
+    frac = eps / eps.sum()
+    ne_ = len(frac)
+    ns = np.asarray(eos.n_stages)
+    J = np.asarray(eos.lnU).shape[1]          # stage columns of the tables (I .. V)
+    U = partition_functions(eos, T)
+    kT = K_BOLTZ * T
+    saha = (2.0 * math.pi * M_ELECTRON * kT / H_PLANCK ** 2) ** 1.5
+    phi = np.zeros((ne_, max(J - 1, 1)))
+    for e in range(ne_):
+        for j in range(ns[e] - 1):
+            phi[e, j] = 2.0 * U[e, j + 1] / U[e, j] * saha * math.exp(-eos.chi_eV[e, j] / (K_EV * T))
+    n_tot = P / kT
+    charge = np.arange(J, dtype=np.float64)
+
+    def stage_factors(n_e):
+        # r[e, j] = prod_{i<j} Phi_{e,i} / n_e (r[e, 0] = 1; zero beyond the last stage)
+        r = np.zeros((ne_, J))
+        r[:, 0] = 1.0
+        for j in range(1, J):
+            r[:, j] = np.where(j < ns, r[:, j - 1] * phi[:, j - 1] / n_e, 0.0)
+        return r
+
+    # start: electrons from hydrogen alone (closed form of the pure-H Saha balance), neutrals
+    # from the stage factors at that n_e
+    x = math.sqrt(phi[0, 0] * kT / (P + phi[0, 0] * kT)) if phi[0, 0] > 0 else 1e-10
+    n_e = max(x * n_tot / (1.0 + x), 1e-30 * n_tot)
+    r = stage_factors(n_e)
+    n0 = frac * (n_tot - n_e) / r.sum(axis=1)
+    for _ in range(max_iter):
+        r = stage_factors(n_e)
+        s0 = r.sum(axis=1)                      # sum_j r_j
+        s1 = r @ charge                         # sum_j j r_j
+        s2 = r @ (charge * charge)              # sum_j j^2 r_j
+        n_nuc = n_tot - n_e
+        f = np.empty(ne_ + 1)
+        f[:ne_] = n0 * s0 - frac * n_nuc
+        f[ne_] = np.dot(n0, s1) - n_e
+        M = np.zeros((ne_ + 1, ne_ + 1))
+        M[np.arange(ne_), np.arange(ne_)] = s0                 # d f_e / d n_{e,0}
+        M[:ne_, ne_] = -n0 * s1 / n_e + frac                    # d f_e / d n_e (d r_j / d n_e = -j r_j / n_e)
+        M[ne_, :ne_] = s1                                       # d f_ele / d n_{e,0}
+        M[ne_, ne_] = -np.dot(n0, s2) / n_e - 1.0               # d f_ele / d n_e
+        dn = lu_solve(lu_factor(M), -f)
+        cur = np.r_[n0, n_e]
+        lam = 1.0
+        neg = dn < -0.9 * cur
+        if np.any(neg):
+            lam = float(np.min(-0.9 * cur[neg] / dn[neg]))
+        new = cur + lam * dn
+        rel = np.abs(lam * dn) / np.maximum(np.abs(cur), 1e-300)
+        n0, n_e = new[:ne_], float(new[ne_])
+        if rel.max() < tol:
+            break
+    r = stage_factors(n_e)
+    n_nuc = n_tot - n_e
+    stage = n0[:, None] * r
+    NU = np.where(U > 0, stage / np.where(U > 0, U, 1.0), 0.0)
+    rho = n_nuc * float(np.sum(frac * np.asarray(eos.mass_amu) * AMU))
+    return Populations(T, P, n_e, n_nuc, float(stage[0, 0]), rho, stage, NU)
+
+
 @dataclass
 class LineTerms:
     """Per-line quantities of Eq. (l_nu_line) at one (T, P) point."""

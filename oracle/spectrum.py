@@ -63,8 +63,10 @@ def formal_solution(tau, S, mu):
 
 
 def spectrum(lines, species_el, species_stage, el, m, T, P, win_grid, mus, cut=1e-3, kc_factor=1e-2,
-             abund_scale=None, vturb=0.0):
-    """I[n_mu][N_win] of one atmosphere over a window grid (FP64, dense)."""
+             abund_scale=None, vturb=0.0, continuum=None):
+    """I[n_mu][N_win] of one atmosphere over a window grid (FP64, dense).  continuum: None for the
+    flat continuum of the cut rule, or a tuple of continuum.kappa_c sources added per wavelength
+    instead (the cut keeps the flat continuum)."""
     D = len(m)
     N = synthesis.grid_size(win_grid.lam0_nm, win_grid.lam1_nm, win_grid.R)
     kap = np.empty((D, N))
@@ -74,7 +76,7 @@ def spectrum(lines, species_el, species_stage, el, m, T, P, win_grid, mus, cut=1
         pl = synthesis.prepare(lines, species_el, species_stage, el, T[d], P[d], win_grid, cut, kc_factor,
                                abund_scale, vturb)
         k, _, _ = synthesis.kappa_dense(pl)
-        kap[d] = k + pl.kappa_c
+        kap[d] = k + (pl.kappa_c if continuum is None else _continuum(lam_cm, pl.pop, el, T[d], continuum))
         S[d] = planck_lambda(lam_cm, T[d])
     out = np.empty((len(mus), N))
     for j in range(N):
@@ -84,8 +86,15 @@ def spectrum(lines, species_el, species_stage, el, m, T, P, win_grid, mus, cut=1
     return out
 
 
+def _continuum(lam_cm, pop, el, T, sources):
+    # closed-form continuum at the grid wavelengths; U_HI of the element table at T
+    from . import continuum, physics as ph
+    U_HI = float(ph.partition_functions(el, T)[0, 0]) if hasattr(el, "n_stages") else float(el.U1[0])
+    return continuum.kappa_c(np.asarray(lam_cm) * 1e7, pop, U_HI=U_HI, sources=sources)
+
+
 def spectrum_at(lines, species_el, species_stage, el, m, T, P, win_grid, mus, js, cut=1e-3, kc_factor=1e-2,
-                abund_scale=None, vturb=0.0, slack_band=3e-5):
+                abund_scale=None, vturb=0.0, slack_band=3e-5, continuum=None):
     """I[n_mu][len(js)] of one atmosphere at the window grid indices js only (same steps as
     `spectrum`; the opacity of each depth comes from synthesis.kappa_at), together with a bound
     on how far I can move when contributions inside the edge-slack band of the cut are taken
@@ -101,7 +110,7 @@ def spectrum_at(lines, species_el, species_stage, el, m, T, P, win_grid, mus, js
         pl = synthesis.prepare(lines, species_el, species_stage, el, T[d], P[d], win_grid, cut, kc_factor,
                                abund_scale, vturb)
         k, s = synthesis.kappa_at(pl, js, slack_band)
-        kap[d] = k + pl.kappa_c
+        kap[d] = k + (pl.kappa_c if continuum is None else _continuum(lam_cm, pl.pop, el, T[d], continuum))
         sl[d] = s
         S[d] = planck_lambda(lam_cm, T[d])
     out = np.empty((len(mus), len(js)))

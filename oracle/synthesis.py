@@ -57,7 +57,9 @@ def lower_median(x: np.ndarray) -> float:
 
 def prepare(lines, species_el, species_stage, el, T, P, grid, cut=1e-3, kc_factor=1e-2,
             abund_scale=None, vturb=0.0) -> PointLines:
-    pop = physics.populations(T, P, el, abund_scale)
+    # an element table with stages beyond II (n_stages) takes the multi-stage equation of state
+    pop = physics.populations_eos(T, P, el, abund_scale) if hasattr(el, "n_stages") else \
+        physics.populations(T, P, el, abund_scale)
     terms = physics.line_terms(lines, species_el, species_stage, el, pop, vturb)
     kappa0 = terms.S * H(0.0, terms.a)
     kc = kc_factor * lower_median(kappa0)

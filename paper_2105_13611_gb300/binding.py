@@ -24,9 +24,10 @@ EXPORTED = ["mpsa_create", "mpsa_destroy", "mpsa_last_error", "mpsa_version", "m
             "mpsa_server_create", "mpsa_server_submit", "mpsa_server_wait", "mpsa_server_get_stats",
             "mpsa_server_destroy", "mpsa_server_cancel_queued",
             "mpsa_batch_create", "mpsa_batch_run", "mpsa_batch_get_info", "mpsa_batch_destroy", "mpsa_voigt",
-            "odf_intensity"]
+            "odf_intensity", "set_atmosphere_grid_eos", "mpsa_get_populations", "synth_continuum"]
 REQ_SPECTRUM, REQ_ODF = 1, 2
-KERNEL_PROFILE, KERNEL_ODF, KERNEL_BINS = 0, 1, 2
+KERNEL_PROFILE, KERNEL_ODF, KERNEL_BINS, KERNEL_CONTINUUM = 0, 1, 2, 3
+CONT_ELEC, CONT_HBF, CONT_HFF, CONT_HRAY, CONT_ALL = 1, 2, 4, 8, 15
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -36,6 +37,11 @@ _ip = C.POINTER(C.c_int32)
 class Elements(C.Structure):
     _fields_ = [("n_elements", C.c_int32), ("mass_amu", _dp), ("chi_eV", _dp), ("U1", _dp), ("U2", _dp),
                 ("log_eps", _dp)]
+
+
+class Eos(C.Structure):
+    _fields_ = [("n_elements", C.c_int32), ("mass_amu", _dp), ("log_eps", _dp), ("n_stages", _ip), ("chi_eV", _dp),
+                ("lnU", _dp)]
 
 
 class Lines(C.Structure):
@@ -48,7 +54,8 @@ class LGrid(C.Structure):
 
 
 class SynthOpts(C.Structure):
-    _fields_ = [("cut", C.c_double), ("kc_factor", C.c_double), ("precision", C.c_int32), ("tile", C.c_int32)]
+    _fields_ = [("cut", C.c_double), ("kc_factor", C.c_double), ("precision", C.c_int32), ("tile", C.c_int32),
+                ("continuum", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Atmos(C.Structure):
@@ -109,6 +116,12 @@ def load_library(path: str = LIB_PATH):
     lib.mpsa_destroy.restype = None
     lib.mpsa_last_error.restype = C.c_char_p
     lib.mpsa_version.restype = C.c_char_p
+    lib.set_atmosphere_grid_eos.argtypes = [vp, C.POINTER(Eos), C.c_int32, _dp, _dp, C.c_int32, _dp, C.c_double]
+    lib.set_atmosphere_grid_eos.restype = C.c_int
+    lib.mpsa_get_populations.argtypes = [vp, C.c_int32, C.c_int32, _dp, _ip]
+    lib.mpsa_get_populations.restype = C.c_int
+    lib.synth_continuum.argtypes = [vp, C.POINTER(LGrid), C.c_int32, _ip, C.c_int32, vp, vp]
+    lib.synth_continuum.restype = C.c_int
     lib.mpsa_grid_size.argtypes = [C.POINTER(LGrid)]
     lib.mpsa_grid_size.restype = C.c_int64
     lib.load_linelist.argtypes = [vp, C.c_int32, _ip, _ip, C.POINTER(Lines)]
@@ -189,8 +202,8 @@ def grid_size(lam0_nm, lam1_nm, R) -> int:
     return int(lib.mpsa_grid_size(C.byref(LGrid(lam0_nm, lam1_nm, R))))
 
 
-def make_opts(cut=1e-3, kc_factor=1e-2, precision=PREC_FP32_COMPENSATED):
-    return SynthOpts(cut, kc_factor, precision, 0)
+def make_opts(cut=1e-3, kc_factor=1e-2, precision=PREC_FP32_COMPENSATED, continuum=0):
+    return SynthOpts(cut, kc_factor, precision, 0, continuum, 0)
 
 
 def _odf_args(kappa, bounds, widths, odf_out, device):
@@ -281,6 +294,35 @@ class Context:
                                             n_comp, _ptr(ab, C.c_double) if ab is not None else None, float(vturb)))
         self.n_points = len(T)
 
+    def set_atmosphere_grid_eos(self, eos, T, P, abund_scale=None, vturb=0.0):
+        """eos: workloads.EosTable (multi-stage table); T, P, abund_scale as for set_atmosphere_grid."""
+        n = eos.n
+        arrs = [_arr(eos.mass_amu, np.float64), _arr(eos.log_eps, np.float64)]
+        ns = _arr(eos.n_stages, np.int32)
+        chi = _arr(np.asarray(eos.chi_eV).reshape(n, 4), np.float64)
+        lnU = _arr(np.asarray(eos.lnU).reshape(n, 5, 3), np.float64)
+        E = Eos(n, _ptr(arrs[0], C.c_double), _ptr(arrs[1], C.c_double), _ptr(ns, C.c_int32), _ptr(chi, C.c_double),
+                _ptr(lnU, C.c_double))
+        T = _arr(T, np.float64)
+        P = _arr(P, np.float64)
+        if abund_scale is None:
+            n_comp, ab = 1, None
+        else:
+            ab = _arr(abund_scale, np.float64)
+            n_comp = ab.shape[0]
+        _check(self.lib.set_atmosphere_grid_eos(self.h, C.byref(E), len(T), _ptr(T, C.c_double), _ptr(P, C.c_double),
+                                                n_comp, _ptr(ab, C.c_double) if ab is not None else None, float(vturb)))
+        self.n_points = len(T)
+
+    def get_populations(self, row0, n_rows):
+        """Rows of the FP64 population table as a numpy array [n_rows][5 + 5 n_elements]: T, P, n_e,
+        n_HI, rho, then N/U of stages I..V of every element."""
+        st = C.c_int32()
+        _check(self.lib.mpsa_get_populations(self.h, int(row0), 0, None, C.byref(st)))
+        out = np.empty((int(n_rows), st.value), dtype=np.float64)
+        _check(self.lib.mpsa_get_populations(self.h, int(row0), int(n_rows), _ptr(out, C.c_double), C.byref(st)))
+        return out
+
     def synth_opacity(self, grid, sel, kappa_out, kappa_c_out=None, evals_out=None, opts=None, stream=None):
         s = _arr(sel, np.int32)
         g = LGrid(grid.lam0_nm, grid.lam1_nm, grid.R)
@@ -292,6 +334,14 @@ class Context:
         b, w, n_rows, N = _odf_args(kappa, bounds, widths, odf_out, self.device)
         _check(self.lib.build_odf(self.h, _dev(kappa), n_rows, N, len(b) - 1, _ptr(b, C.c_int64), len(w),
                                   _ptr(w, C.c_double), mean_kind, _dev(odf_out), _stream(stream)))
+
+    def synth_continuum(self, grid, sel, kappa_out, sources=CONT_ALL, stream=None):
+        """Closed-form continuum (synth_continuum in include/mpsa.h) of rows sel on grid into the
+        float32 CUDA tensor kappa_out [len(sel)][N]."""
+        s_ = _arr(sel, np.int32)
+        g = LGrid(grid.lam0_nm, grid.lam1_nm, grid.R)
+        _check(self.lib.synth_continuum(self.h, C.byref(g), len(s_), _ptr(s_, C.c_int32), int(sources),
+                                        _dev(kappa_out), _stream(stream)))
 
     def voigt(self, v, a, out, precision=0, stream=None):
         """H(v, a) on the device as the kernels evaluate it; v, a, out: device float64 tensors."""

@@ -49,59 +49,101 @@ int upload(T** dst, const T* src, size_t n) {
     return MPSA_OK;
 }
 
-// Saha charge balance for one (composition, point) row, FP64.
-// Particle conservation P = (n_nuc + n_e) kT; each element ionises once with
-// n_II = f n_nuc Phi / (n_e + Phi), Phi = (2 U_II/U_I)(2 pi m_e kT/h^2)^{3/2} e^{-chi/kT};
-// charge conservation n_e = sum n_II is solved for n_e by bisection in ln n_e
-// (g(n_e) = n_e - sum n_II(n_e) is increasing on (0, P/kT)).
+// The LTE equation of state of one (composition, point) row, FP64 (paper App. A, without
+// molecules).  Element e has stages j = 0 .. J_e - 1 linked by the Saha-Boltzmann ratio
+//   n_{e,j+1} n_e / n_{e,j} = Phi_{e,j} = (2 U_{j+1}/U_j) (2 pi m_e k T/h^2)^{3/2} e^{-chi_j/kT},
+// U_j(T) = exp(c0 + c1 x + c2 x^2), x = ln(T / 5040 K).  Particle conservation gives
+// n_nuc = P/kT - n_e, and charge conservation n_e = n_nuc sum_e a_e <j>_e(n_e), <j>_e the
+// mean charge of element e at that n_e.  g(y) = n_e - n_nuc sum_e a_e <j>_e with y = ln n_e is
+// increasing (dg/dn_e = 1 + Q + n_nuc sum_e a_e Var_e / n_e > 0), so the root is unique; it
+// is found by Newton steps in y kept inside a shrinking bracket (bisection where a step would
+// leave it), to a relative change of n_e below 1e-14.  The stage weights prod_{i<j} Phi_i / n_e
+// are formed in log space and scaled by their largest value, so no ratio overflows.
 __global__ void k_populations(int rows, int n_points, int n_el, const double* __restrict__ el,
                               const double* __restrict__ abund, const double* __restrict__ T,
                               const double* __restrict__ P, double* __restrict__ pop) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     const int comp = r / n_points, pt = r % n_points;
     const double t = T[pt], p = P[pt];
-    const double* mass = el;
-    const double* chi = el + n_el;
-    const double* U1 = el + 2 * n_el;
-    const double* U2 = el + 3 * n_el;
-    const double* leps = el + 4 * n_el;
     const double kT = kKB * t;
-    const double saha = pow(2.0 * kPI * kME * kT / (kH * kH), 1.5);
+    const double lsaha = 1.5 * log(2.0 * kPI * kME * kT / (kH * kH));
+    const double x = log(t / 5040.0);
     double* row = pop + (size_t)r * pop_stride(n_el);
-    // number fractions
     double eps_sum = 0.0;
-    for (int e = 0; e < n_el; ++e) eps_sum += pow(10.0, leps[e] - 12.0) * abund[(size_t)comp * n_el + e];
+    for (int e = 0; e < n_el; ++e) eps_sum += pow(10.0, el[e * kElStride + kElLogEps] - 12.0) * abund[(size_t)comp * n_el + e];
+    double frac[64];
+    double lphi[64][kMaxStages - 1];   // ln Phi_{e,j}
+    double lU[64][kMaxStages];          // ln U_{e,j}
+    int ns[64];
+    for (int e = 0; e < n_el; ++e) {
+        const double* q = el + e * kElStride;
+        frac[e] = pow(10.0, q[kElLogEps] - 12.0) * abund[(size_t)comp * n_el + e] / eps_sum;
+        ns[e] = (int)q[kElStages];
+        for (int j = 0; j < ns[e]; ++j) {
+            const double* c = q + kElLnU + 3 * j;
+            lU[e][j] = c[0] + x * (c[1] + x * c[2]);
+        }
+        for (int j = 0; j + 1 < ns[e]; ++j)
+            lphi[e][j] = 0.69314718055994530942 + lU[e][j + 1] - lU[e][j] + lsaha - q[kElChi + j] * kEV / kT;
+    }
     const double n_tot = p / kT;
-    // per-element number fraction f and Saha factor Phi (hoisted out of the root search)
-    double frac[64], phi[64];
-    for (int e = 0; e < n_el; ++e) {
-        frac[e] = pow(10.0, leps[e] - 12.0) * abund[(size_t)comp * n_el + e] / eps_sum;
-        phi[e] = 2.0 * U2[e] / U1[e] * saha * exp(-chi[e] * kEV / kT);
+    // stage weights of element e at y = ln n_e: w_j = exp(lp_j - max lp), lp_j = sum_{i<j} (ln Phi_i - y)
+    auto weights = [&](int e, double y, double* w) -> double {
+        double lp[kMaxStages], mx = 0.0;
+        lp[0] = 0.0;
+        for (int j = 1; j < ns[e]; ++j) {
+            lp[j] = lp[j - 1] + lphi[e][j - 1] - y;
+            mx = fmax(mx, lp[j]);
+        }
+        double s0 = 0.0;
+        for (int j = 0; j < ns[e]; ++j) {
+            w[j] = exp(lp[j] - mx);
+            s0 += w[j];
+        }
+        return s0;
+    };
+    // g(y) and dg/dy
+    auto eval = [&](double y, double* g, double* dg) {
+        const double ne = exp(y), nn = n_tot - ne;
+        double q = 0.0, v = 0.0;
+        for (int e = 0; e < n_el; ++e) {
+            double w[kMaxStages];
+            const double s0 = weights(e, y, w);
+            double s1 = 0.0, s2 = 0.0;
+            for (int j = 1; j < ns[e]; ++j) {
+                s1 += j * w[j];
+                s2 += (double)j * j * w[j];
+            }
+            const double mean = s1 / s0;
+            q += frac[e] * mean;
+            v += frac[e] * fmax(s2 / s0 - mean * mean, 0.0);
+        }
+        *g = ne - nn * q;
+        *dg = ne * (1.0 + q) + nn * v;
+    };
+    double lo = log(1e-300), hi = log(n_tot), y = 0.5 * (lo + hi);
+    for (int it = 0; it < 400; ++it) {
+        double g, dg;
+        eval(y, &g, &dg);
+        if (g > 0.0) hi = y; else lo = y;
+        double yn = (dg > 0.0) ? y - g / dg : 0.5 * (lo + hi);
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+        const double dy = yn - y;
+        y = yn;
+        if (fabs(dy) < 1e-14 || !(hi - lo > 0.0) || !(y > lo && y < hi && (0.5 * (lo + hi) != lo))) break;
     }
-    // bisection in ln n_e down to adjacent doubles: stop when the midpoint no longer lies
-    // strictly between the bounds (a fixed width such as 1e-15 is below one ulp of ln n_e
-    // for |ln n_e| > 4 and would never be reached)
-    double lo = log(1e-300), hi = log(n_tot);
-    for (int it = 0; it < 2000; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        const double ne = exp(mid), nn = n_tot - ne;
-        double ion = 0.0;
-        for (int e = 0; e < n_el; ++e) ion += frac[e] * nn * phi[e] / (ne + phi[e]);
-        if (ne - ion > 0.0) hi = mid; else lo = mid;
-    }
-    const double ne = exp(0.5 * (lo + hi)), nn = n_tot - ne;
-    double mmean = 0.0;
-    double nHI = 0.0;
+    const double ne = exp(y), nn = n_tot - ne;
+    double mmean = 0.0, nHI = 0.0;
     for (int e = 0; e < n_el; ++e) {
-        // n_II/n_I = Phi/n_e; n_I = f n n_e/(n_e + Phi) has no cancellation for a fully ionised stage I
-        const double n2 = frac[e] * nn * phi[e] / (ne + phi[e]);
-        const double n1 = frac[e] * nn * ne / (ne + phi[e]);
-        row[kPopHdr + 2 * e] = n1 / U1[e];
-        row[kPopHdr + 2 * e + 1] = n2 / U2[e];
-        mmean += frac[e] * mass[e] * kAMU;
-        if (e == 0) nHI = n1;
+        double w[kMaxStages];
+        const double s0 = weights(e, y, w);
+        for (int j = 0; j < kMaxStages; ++j) {
+            const double nj = j < ns[e] ? frac[e] * nn * w[j] / s0 : 0.0;
+            row[pop_nu(e, j)] = j < ns[e] ? nj / exp(lU[e][j]) : 0.0;
+            if (e == 0 && j == 0) nHI = nj;
+        }
+        mmean += frac[e] * el[e * kElStride + kElMass] * kAMU;
     }
     row[kPopT] = t;
     row[kPopP] = p;
@@ -141,8 +183,22 @@ int mpsa_create(mpsa_ctx** out, int device) {
     if (rc != MPSA_OK) return rc;
     rc = spectrum_module_init(device);
     if (rc != MPSA_OK) return rc;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    MPSA_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;   // keep freed scratch cached until the context goes
+    cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return fail(MPSA_ECUDA, "mpsa_create: memory pool: %s", cudaGetErrorString(e));
+    }
     mpsa_ctx* c = new mpsa_ctx();
     c->device = device;
+    c->pool = pool;
     *out = c;
     return MPSA_OK;
 }
@@ -157,6 +213,7 @@ void mpsa_destroy(mpsa_ctx* c) {
                     c->d_lgS, c->d_lgW, c->d_species, c->d_pop};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     delete c;
 }
 
@@ -177,7 +234,7 @@ int load_linelist(mpsa_ctx* c, int32_t n_species, const int32_t* sp_el, const in
     if (!ln->lambda_nm || !ln->log_gf || !ln->E_eV || !ln->species || !ln->log_gR || !ln->log_gS || !ln->log_gW)
         return fail(MPSA_EINVAL, "load_linelist: NULL line array");
     for (int s = 0; s < n_species; ++s)
-        if (sp_el[s] < 0 || sp_stage[s] < 0 || sp_stage[s] > 1)
+        if (sp_el[s] < 0 || sp_stage[s] < 0 || sp_stage[s] >= kMaxStages)
             return fail(MPSA_EINVAL, "load_linelist: species %d has element %d stage %d", s, sp_el[s], sp_stage[s]);
     for (int64_t i = 0; i < L; ++i) {
         const double lam = ln->lambda_nm[i];
@@ -207,41 +264,32 @@ int load_linelist(mpsa_ctx* c, int32_t n_species, const int32_t* sp_el, const in
     return MPSA_OK;
 }
 
-int set_atmosphere_grid(mpsa_ctx* c, const mpsa_elements* el, int32_t n_points, const double* T, const double* P,
-                        int32_t n_comp, const double* abund, double vturb) {
-    if (!c || !el || !T || !P) return fail(MPSA_EINVAL, "set_atmosphere_grid: NULL argument");
-    const int ne = el->n_elements;
-    if (ne < 1 || ne > 64) return fail(MPSA_EINVAL, "set_atmosphere_grid: n_elements = %d", ne);
-    if (!el->mass_amu || !el->chi_eV || !el->U1 || !el->U2 || !el->log_eps)
-        return fail(MPSA_EINVAL, "set_atmosphere_grid: NULL element array");
-    if (n_points < 1) return fail(MPSA_EINVAL, "set_atmosphere_grid: n_points = %d", n_points);
-    if (n_comp < 1 || (!abund && n_comp != 1)) return fail(MPSA_EINVAL, "set_atmosphere_grid: n_comp = %d", n_comp);
-    if (!(vturb >= 0) || !isfinite(vturb)) return fail(MPSA_EINVAL, "set_atmosphere_grid: vturb = %g", vturb);
+}  // extern "C"
+
+namespace mpsa {
+namespace {
+
+// Population table of every (composition, point) row from packed element records (shared by
+// set_atmosphere_grid and set_atmosphere_grid_eos).
+int atmosphere_grid(mpsa_ctx* c, const char* who, int ne, const std::vector<double>& rec, int32_t n_points,
+                    const double* T, const double* P, int32_t n_comp, const double* abund, double vturb) {
+    if (n_points < 1) return fail(MPSA_EINVAL, "%s: n_points = %d", who, n_points);
+    if (n_comp < 1 || (!abund && n_comp != 1)) return fail(MPSA_EINVAL, "%s: n_comp = %d", who, n_comp);
+    if (!(vturb >= 0) || !isfinite(vturb)) return fail(MPSA_EINVAL, "%s: vturb = %g", who, vturb);
+    if ((int64_t)n_comp * n_points > (1ll << 30)) return fail(MPSA_EINVAL, "%s: %d x %d rows", who, n_comp, n_points);
     for (int i = 0; i < n_points; ++i)
         if (!(T[i] > 0) || !(P[i] > 0) || !isfinite(T[i]) || !isfinite(P[i]))
-            return fail(MPSA_EINVAL, "set_atmosphere_grid: T[%d] = %g, P[%d] = %g", i, T[i], i, P[i]);
-    for (int e = 0; e < ne; ++e)
-        if (!(el->mass_amu[e] > 0) || !(el->U1[e] > 0) || !(el->U2[e] > 0) || !isfinite(el->chi_eV[e]) ||
-            !isfinite(el->log_eps[e]))
-            return fail(MPSA_EINVAL, "set_atmosphere_grid: bad element %d", e);
+            return fail(MPSA_EINVAL, "%s: T[%d] = %g, P[%d] = %g", who, i, T[i], i, P[i]);
     std::vector<double> ab((size_t)n_comp * ne, 1.0);
     if (abund)
         for (size_t i = 0; i < ab.size(); ++i) {
-            if (!(abund[i] >= 0) || !isfinite(abund[i])) return fail(MPSA_EINVAL, "set_atmosphere_grid: abund[%zu]", i);
+            if (!(abund[i] >= 0) || !isfinite(abund[i])) return fail(MPSA_EINVAL, "%s: abund[%zu]", who, i);
             ab[i] = abund[i];
         }
-    std::vector<double> h(5 * ne);
-    for (int e = 0; e < ne; ++e) {
-        h[e] = el->mass_amu[e];
-        h[ne + e] = el->chi_eV[e];
-        h[2 * ne + e] = el->U1[e];
-        h[3 * ne + e] = el->U2[e];
-        h[4 * ne + e] = el->log_eps[e];
-    }
     MPSA_CUDA_TRY(cudaSetDevice(c->device));
     int rc;
     double *dT = nullptr, *dP = nullptr, *dab = nullptr;
-    if ((rc = upload(&c->d_el, h.data(), h.size()))) return rc;
+    if ((rc = upload(&c->d_el, rec.data(), rec.size()))) return rc;
     if ((rc = upload(&dT, T, n_points)) || (rc = upload(&dP, P, n_points)) || (rc = upload(&dab, ab.data(), ab.size()))) {
         cudaFree(dT), cudaFree(dP), cudaFree(dab);
         return rc;
@@ -251,19 +299,97 @@ int set_atmosphere_grid(mpsa_ctx* c, const mpsa_elements* el, int32_t n_points, 
     cudaError_t e = cudaMalloc(&c->d_pop, rows * pop_stride(ne) * sizeof(double));
     if (e != cudaSuccess) {
         cudaFree(dT), cudaFree(dP), cudaFree(dab);
-        return fail(MPSA_ENOMEM, "set_atmosphere_grid: %s", cudaGetErrorString(e));
+        c->n_el = 0;
+        return fail(MPSA_ENOMEM, "%s: %s", who, cudaGetErrorString(e));
     }
     rc = populations_device(ne, c->d_el, dab, n_comp, n_points, dT, dP, c->d_pop, 0);
     cudaError_t e2 = cudaDeviceSynchronize();
     cudaFree(dT), cudaFree(dP), cudaFree(dab);
     if (rc) return rc;
-    if (e2 != cudaSuccess) return fail(MPSA_ECUDA, "set_atmosphere_grid: %s", cudaGetErrorString(e2));
+    if (e2 != cudaSuccess) return fail(MPSA_ECUDA, "%s: %s", who, cudaGetErrorString(e2));
     c->n_el = ne;
-    c->h_el = h;
+    c->h_el = rec;
     c->n_points = n_points;
     c->n_comp = n_comp;
     c->vturb = vturb;
     c->h_abund = ab;
+    return MPSA_OK;
+}
+
+}  // namespace
+}  // namespace mpsa
+
+extern "C" {
+
+int set_atmosphere_grid(mpsa_ctx* c, const mpsa_elements* el, int32_t n_points, const double* T, const double* P,
+                        int32_t n_comp, const double* abund, double vturb) {
+    if (!c || !el || !T || !P) return fail(MPSA_EINVAL, "set_atmosphere_grid: NULL argument");
+    const int ne = el->n_elements;
+    if (ne < 1 || ne > 64) return fail(MPSA_EINVAL, "set_atmosphere_grid: n_elements = %d", ne);
+    if (!el->mass_amu || !el->chi_eV || !el->U1 || !el->U2 || !el->log_eps)
+        return fail(MPSA_EINVAL, "set_atmosphere_grid: NULL element array");
+    for (int e = 0; e < ne; ++e)
+        if (!(el->mass_amu[e] > 0) || !(el->U1[e] > 0) || !(el->U2[e] > 0) || !isfinite(el->chi_eV[e]) ||
+            !isfinite(el->log_eps[e]))
+            return fail(MPSA_EINVAL, "set_atmosphere_grid: bad element %d", e);
+    // the single-ionisation table is the two-stage case with constant partition functions
+    std::vector<double> rec((size_t)ne * kElStride, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        double* q = rec.data() + (size_t)e * kElStride;
+        q[kElMass] = el->mass_amu[e];
+        q[kElLogEps] = el->log_eps[e];
+        q[kElStages] = 2.0;
+        q[kElChi] = el->chi_eV[e];
+        q[kElLnU] = log(el->U1[e]);
+        q[kElLnU + 3] = log(el->U2[e]);
+    }
+    return atmosphere_grid(c, "set_atmosphere_grid", ne, rec, n_points, T, P, n_comp, abund, vturb);
+}
+
+int set_atmosphere_grid_eos(mpsa_ctx* c, const mpsa_eos* eos, int32_t n_points, const double* T, const double* P,
+                            int32_t n_comp, const double* abund, double vturb) {
+    if (!c || !eos || !T || !P) return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: NULL argument");
+    const int ne = eos->n_elements;
+    if (ne < 1 || ne > 64) return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: n_elements = %d", ne);
+    if (!eos->mass_amu || !eos->log_eps || !eos->n_stages || !eos->chi_eV || !eos->lnU)
+        return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: NULL element array");
+    std::vector<double> rec((size_t)ne * kElStride, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        const int ns = eos->n_stages[e];
+        if (!(eos->mass_amu[e] > 0) || !isfinite(eos->mass_amu[e]) || !isfinite(eos->log_eps[e]) || ns < 1 ||
+            ns > kMaxStages)
+            return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: bad element %d", e);
+        double* q = rec.data() + (size_t)e * kElStride;
+        q[kElMass] = eos->mass_amu[e];
+        q[kElLogEps] = eos->log_eps[e];
+        q[kElStages] = ns;
+        for (int j = 0; j + 1 < ns; ++j) {
+            const double chi = eos->chi_eV[(size_t)e * (kMaxStages - 1) + j];
+            if (!isfinite(chi)) return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: chi of element %d stage %d", e, j);
+            q[kElChi + j] = chi;
+        }
+        for (int j = 0; j < ns; ++j)
+            for (int k = 0; k < 3; ++k) {
+                const double v = eos->lnU[((size_t)e * kMaxStages + j) * 3 + k];
+                if (!isfinite(v)) return fail(MPSA_EINVAL, "set_atmosphere_grid_eos: lnU of element %d stage %d", e, j);
+                q[kElLnU + 3 * j + k] = v;
+            }
+    }
+    return atmosphere_grid(c, "set_atmosphere_grid_eos", ne, rec, n_points, T, P, n_comp, abund, vturb);
+}
+
+int mpsa_get_populations(mpsa_ctx* c, int32_t row0, int32_t n_rows, double* out, int32_t* stride) {
+    if (!c || (n_rows > 0 && !out)) return fail(MPSA_EINVAL, "mpsa_get_populations: NULL argument");
+    if (!c->d_pop) return fail(MPSA_ESTATE, "mpsa_get_populations: no atmosphere grid set");
+    const int rows = c->n_comp * c->n_points;
+    if (row0 < 0 || n_rows < 0 || row0 + (int64_t)n_rows > rows)
+        return fail(MPSA_EINVAL, "mpsa_get_populations: rows %d..%d of %d", row0, row0 + n_rows, rows);
+    const int st = pop_stride(c->n_el);
+    if (stride) *stride = st;
+    if (n_rows == 0) return MPSA_OK;
+    MPSA_CUDA_TRY(cudaSetDevice(c->device));
+    MPSA_CUDA_TRY(cudaMemcpy(out, c->d_pop + (size_t)row0 * st, (size_t)n_rows * st * sizeof(double),
+                             cudaMemcpyDeviceToHost));
     return MPSA_OK;
 }
 
@@ -274,7 +400,7 @@ int mpsa_profile_enable(mpsa_ctx* c, int enable) {
 }
 
 int mpsa_profile_read(mpsa_ctx* c, int kernel, double* total_ms, int64_t* launches) {
-    if (!c || !total_ms || !launches || kernel < 0 || kernel > 2) return fail(MPSA_EINVAL, "mpsa_profile_read: bad argument");
+    if (!c || !total_ms || !launches || kernel < 0 || kernel > 3) return fail(MPSA_EINVAL, "mpsa_profile_read: bad argument");
     auto& v = c->prof_ev[kernel];
     double tot = 0.0;
     int64_t n = 0;

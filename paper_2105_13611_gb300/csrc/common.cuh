@@ -23,9 +23,17 @@ constexpr double kEV = 1.602176634e-12;          // electron volt [erg]
 constexpr double kPI = 3.14159265358979323846;
 
 // Layout of one population-table row (FP64): T, P, n_e, n_HI, rho, then N/U of
-// stages I and II of every element.
+// stages I .. V of every element (0 for stages an element does not have).
+constexpr int kMaxStages = 5;
 constexpr int kPopT = 0, kPopP = 1, kPopNe = 2, kPopNHI = 3, kPopRho = 4, kPopHdr = 5;
-__host__ __device__ inline int pop_stride(int n_el) { return kPopHdr + 2 * n_el; }
+__host__ __device__ inline int pop_stride(int n_el) { return kPopHdr + kMaxStages * n_el; }
+__host__ __device__ inline int pop_nu(int e, int stage) { return kPopHdr + kMaxStages * e + stage; }
+
+// Element record of the equation of state (FP64, kElStride values per element): mass [amu],
+// log eps (H = 12), number of stages (1..5), ionisation energies chi_0..chi_3 [eV] (stage j ->
+// j + 1) and the partition-function coefficients ln U_j(T) = c0 + c1 x + c2 x^2 of stages
+// 0..4, x = ln(T / 5040 K).
+constexpr int kElMass = 0, kElLogEps = 1, kElStages = 2, kElChi = 3, kElLnU = 7, kElStride = 22;
 
 // Grid points per tile of the profile kernel and threads per tile.
 constexpr int kTileThreads = 256;
@@ -45,16 +53,19 @@ int fail(int code, const char* fmt, ...);
                                 "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-// Stream-ordered scratch buffer: allocated with cudaMallocAsync on the call's
-// stream and released with cudaFreeAsync on the same stream.
+// Stream-ordered scratch buffer: allocated on the call's stream from the context's
+// memory pool (cudaMallocFromPoolAsync; the device's default pool without a pool) and
+// released with cudaFreeAsync on the same stream.
 struct Scratch {
     std::vector<void*> ptrs;
     cudaStream_t stream = nullptr;
-    explicit Scratch(cudaStream_t s) : stream(s) {}
+    cudaMemPool_t pool = nullptr;
+    explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr) : stream(s), pool(p) {}
     template <class T>
     int alloc(T** p, size_t n) {
         void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, n * sizeof(T) + 16, stream);
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, n * sizeof(T) + 16, pool, stream)
+                             : cudaMallocAsync(&q, n * sizeof(T) + 16, stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(MPSA_ENOMEM, "cudaMallocAsync(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
@@ -72,9 +83,13 @@ struct Scratch {
 
 struct mpsa_ctx {
     int device = 0;
-    // element table (device: 5 arrays of n_el doubles, packed)
+    // stream-ordered scratch of every call: a pool of this context that keeps freed memory
+    // cached (release threshold: unlimited) until mpsa_destroy, so that repeated calls do
+    // not map and unmap their gigabytes of line-preparation scratch each time
+    cudaMemPool_t pool = nullptr;
+    // element table of the equation of state (device), [n_el][kElStride] records
     int n_el = 0;
-    double* d_el = nullptr;          // [5][n_el]: mass_amu, chi_eV, U1, U2, log_eps
+    double* d_el = nullptr;
     std::vector<double> h_el;        // host copy, same layout
     // species table
     int n_sp = 0;
@@ -97,7 +112,7 @@ struct mpsa_ctx {
     std::vector<double> h_abund;     // [n_comp][n_el]
     // kernel timing (mpsa_profile_enable)
     bool prof = false;
-    std::vector<cudaEvent_t> prof_ev[3];   // start/stop pairs per kernel
+    std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel
 };
 
 namespace mpsa {

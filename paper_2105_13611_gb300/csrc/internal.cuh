@@ -14,6 +14,10 @@ int populations_device(int n_el, const double* d_el, const double* d_abund, int 
 int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
                float* kappa, float* kc_out, int64_t* evals, const mpsa_synth_opts* opts, cudaStream_t st);
 
+// Every species of the line list refers to an element of the table and to a stage that
+// element has (synth.cu).
+int check_species(const mpsa_ctx* ctx, const char* who);
+
 // Validates a grid and returns its point count (synth.cu).
 int check_grid(const mpsa_lgrid* g, int* N);
 
@@ -32,8 +36,14 @@ int odf_setup();
 int odf_check(const char* who, int n_rows, int64_t N, int K, const int64_t* bounds, int n_steps,
               const double* widths, int mean_kind, double* cw);
 
-// Formal solution for D depths on a window grid (spectrum.cu); inputs device-resident.
-int formal_launch(int D, int N, const float* kappa, const float* kc, const float* m, const float* T, double lam0_nm,
-                  double lnq, int n_mu, const float* mu, float* I_out, cudaStream_t st);
+// Continuous opacity of rows d_sel of `pop` on the grid (lam0, R, N) from the MPSA_CONT_* sources
+// into out [n_sel][N] (continuum.cu).
+int continuum_launch(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, double lam0_nm, double R, int N,
+                     int sources, float* out, cudaStream_t st);
+
+// Formal solution for D depths on a window grid (spectrum.cu); inputs device-resident.  The
+// continuum is kc[d] per depth, or kcont[d][j] per depth and wavelength when kcont is not null.
+int formal_launch(int D, int N, const float* kappa, const float* kc, const float* kcont, const float* m,
+                  const float* T, double lam0_nm, double lnq, int n_mu, const float* mu, float* I_out, cudaStream_t st);
 
 }  // namespace mpsa

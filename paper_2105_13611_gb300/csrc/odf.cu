@@ -773,7 +773,7 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
     if ((r = odf_check("build_odf", n_rows, N, K, bounds, n_steps, widths, mean_kind, cw.data()))) return r;
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    Scratch sc(st);
+    Scratch sc(st, ctx->pool);
     int64_t* d_b;
     double *d_cw, *d_w;
     if ((r = sc.alloc(&d_b, K + 1)) || (r = sc.alloc(&d_cw, n_steps + 1)) || (r = sc.alloc(&d_w, n_steps))) return r;
@@ -790,7 +790,7 @@ extern "C" int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int6
 // build_odf_noalloc: build_odf without any device allocation.
 //
 // build_odf stages the interval bounds and the sub-bin widths in stream-ordered
-// scratch (cudaMallocAsync).  This entry point stages them instead in the fixed
+// scratch (the context's pool).  This entry point stages them instead in the fixed
 // file-scope array below, for callers that must not allocate device memory: a
 // process whose device memory is entirely owned by another framework's caching
 // allocator, or a latency-critical loop where an allocation (or a cudaFree that

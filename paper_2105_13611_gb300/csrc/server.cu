@@ -96,7 +96,7 @@ int launch_spectrum(mpsa_server* s, Req* r, Slot& sl) {
     mpsa_ctx* c = s->ctx;
     cudaStream_t st = sl.st;
     const int D = (int)r->m.size(), N = r->N, n_mu = (int)r->mu.size(), ne = c->n_el;
-    Scratch sc(st);
+    Scratch sc(st, s->ctx->pool);
     double *dT, *dP, *dab, *dpop;
     float *fm, *fT, *fmu, *kap, *kc, *Iout;
     int* dsel;
@@ -125,7 +125,8 @@ int launch_spectrum(mpsa_server* s, Req* r, Slot& sl) {
                              nullptr, nullptr, st)))
             return rc;
     }
-    if ((rc = formal_launch(D, N, kap, kc, fm, fT, r->win.lambda0_nm, log1p(1.0 / r->win.R), n_mu, fmu, Iout, st)))
+    if ((rc = formal_launch(D, N, kap, kc, nullptr, fm, fT, r->win.lambda0_nm, log1p(1.0 / r->win.R), n_mu, fmu, Iout,
+                            st)))
         return rc;
     MPSA_CUDA_TRY(cudaMemcpyAsync(sl.pinned, Iout, r->out_bytes, cudaMemcpyDeviceToHost, st));
     return MPSA_OK;
@@ -136,7 +137,7 @@ int launch_odf(mpsa_server* s, Req* r, Slot& sl) {
     cudaStream_t st = sl.st;
     const int n_sel = (int)r->sel.size(), N = r->N, K = (int)r->bounds.size() - 1, ns = (int)r->widths.size();
     const int chunk = std::min(s->rows_per_chunk, n_sel);
-    Scratch sc(st);
+    Scratch sc(st, s->ctx->pool);
     int* dsel;
     float *kap, *kc;
     int64_t* db;

@@ -63,8 +63,8 @@ __device__ __forceinline__ float layer_weight(float x) {
 }
 
 __global__ void k_formal(int D, int N, const float* __restrict__ kappa, const float* __restrict__ kc,
-                         const float* __restrict__ m, const float* __restrict__ T, double lam0_nm, double lnq,
-                         int n_mu, const float* __restrict__ mu, float* __restrict__ I_out) {
+                         const float* __restrict__ kcont, const float* __restrict__ m, const float* __restrict__ T,
+                         double lam0_nm, double lnq, int n_mu, const float* __restrict__ mu, float* __restrict__ I_out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     float tau[kMaxDepth], S[kMaxDepth];
@@ -75,7 +75,8 @@ __global__ void k_formal(int D, int N, const float* __restrict__ kappa, const fl
     const float c2 = (float)(kH * kC / (lam_cm * kKB));
     float kprev = 0.f;
     for (int d = 0; d < D; ++d) {
-        const float k = kappa[(size_t)d * N + j] + kc[d];
+        // continuum: the flat value of the depth, or the closed-form continuum at this wavelength
+        const float k = kappa[(size_t)d * N + j] + (kcont ? kcont[(size_t)d * N + j] : kc[d]);
         tau[d] = d == 0 ? k * m[0] : tau[d - 1] + 0.5f * (kprev + k) * (m[d] - m[d - 1]);
         kprev = k;
         S[d] = planck_f32(c1, lnc1, c2, T[d]);
@@ -303,9 +304,9 @@ unsigned g_spec_init = 0;
 
 }  // namespace
 
-int formal_launch(int D, int N, const float* kappa, const float* kc, const float* m, const float* T, double lam0_nm,
-                  double lnq, int n_mu, const float* mu, float* I_out, cudaStream_t st) {
-    k_formal<<<(N + 127) / 128, 128, 0, st>>>(D, N, kappa, kc, m, T, lam0_nm, lnq, n_mu, mu, I_out);
+int formal_launch(int D, int N, const float* kappa, const float* kc, const float* kcont, const float* m, const float* T,
+                  double lam0_nm, double lnq, int n_mu, const float* mu, float* I_out, cudaStream_t st) {
+    k_formal<<<(N + 127) / 128, 128, 0, st>>>(D, N, kappa, kc, kcont, m, T, lam0_nm, lnq, n_mu, mu, I_out);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }
@@ -337,14 +338,13 @@ extern "C" int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_l
             return fail(MPSA_EINVAL, "synth_spectrum: bad depth %d", d);
         if (d > 0 && !(atm->m[d] > atm->m[d - 1])) return fail(MPSA_EINVAL, "synth_spectrum: m not increasing at %d", d);
     }
-    for (int i = 0; i < ctx->n_sp; ++i)
-        if (ctx->h_sp_el[i] >= ctx->n_el) return fail(MPSA_EINVAL, "synth_spectrum: species/element mismatch");
     int N, r;
+    if ((r = check_species(ctx, "synth_spectrum"))) return r;
     if ((r = check_grid(win, &N))) return r;
     if ((size_t)D * ctx->L >= (size_t)1 << 31) return fail(MPSA_EINVAL, "synth_spectrum: n_depth * n_lines >= 2^31");
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    Scratch sc(st);
+    Scratch sc(st, ctx->pool);
     double *dT, *dP, *dab, *dpop;
     float *fm, *fT, *fmu, *kap, *kc;
     int* dsel;
@@ -367,7 +367,15 @@ extern "C" int synth_spectrum(mpsa_ctx* ctx, const mpsa_atmos* atm, const mpsa_l
     if ((r = populations_device(ne, ctx->d_el, dab, 1, D, dT, dP, dpop, st))) return r;
     k_iota<<<(D + 127) / 128, 128, 0, st>>>(D, dsel);
     if ((r = synth_rows(ctx, dpop, D, dsel, win->lambda0_nm, win->R, N, kap, kc, nullptr, opts, st))) return r;
-    if ((r = formal_launch(D, N, kap, kc, fm, fT, win->lambda0_nm, log1p(1.0 / win->R), n_mu, fmu, I_out, st))) return r;
+    float* kcont = nullptr;
+    const int cont = opts ? opts->continuum : 0;
+    if (cont) {
+        if (cont & ~MPSA_CONT_ALL) return fail(MPSA_EINVAL, "synth_spectrum: continuum = %d", cont);
+        if ((r = sc.alloc(&kcont, (size_t)D * N))) return r;
+        if ((r = continuum_launch(ctx, dpop, D, dsel, win->lambda0_nm, win->R, N, cont, kcont, st))) return r;
+    }
+    if ((r = formal_launch(D, N, kap, kc, kcont, fm, fT, win->lambda0_nm, log1p(1.0 / win->R), n_mu, fmu, I_out, st)))
+        return r;
     // pageable host-to-device copies are staged before cudaMemcpyAsync returns,
     // so the host vectors above may go out of scope now
     return MPSA_OK;
@@ -442,7 +450,7 @@ extern "C" int odf_intensity(mpsa_ctx* ctx, const mpsa_odf_table* tab, int32_t n
         if (!(mu[q] > 0 && mu[q] <= 1)) return fail(MPSA_EINVAL, "odf_intensity: mu[%d] = %g", q, mu[q]);
     MPSA_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
-    Scratch sc(st);
+    Scratch sc(st, ctx->pool);
     const size_t n_tab = (size_t)tab->nT * tab->nP * K * ns, n_cells = (size_t)n_rays * n_depth;
     double *dlt, *dlp, *dw;
     float *dmu, *dtab;

@@ -10,10 +10,10 @@
 //   k_place        per line: centre index c and fraction f on the grid (FP64 log)
 //   k_consts       per (row, species): ln(sqrt(pi) e^2/(m_e c) N/U / rho), u, c/u from the FP64 table
 //   k_kappa0       per (row, line): ln S, a, ln kappa0 in FP32 log space
-//   k_median       per row: lower median of ln kappa0 by radix selection -> ln t_p, kappa_c
+//   k_med_*        per row: lower median of ln kappa0 by multi-CTA radix selection -> ln t_p, kappa_c
 //   k_prep         per (row, line): strength relative to t_p, cut windows (outer: no point
 //                  beyond can pass the cut; inner: every point inside passes), width class
-//   k_scan, k_scatter   stable counting sort of the kept lines by width class
+//   k_scan_class, k_scan_fin, k_scatter   stable counting sort of the kept lines by width class
 //   k_ranges       per (row, class, tile boundary): first line whose centre lies at or
 //                  beyond the boundary (binary search in the centre-sorted class)
 //   k_tiles        the profile kernel: one CTA per (row, 2048-point tile); each thread owns
@@ -79,9 +79,9 @@ __global__ void k_consts(int n_sel, const int* __restrict__ sel, int n_sp, const
     const double* row = pop + (size_t)sel[s] * pop_stride(n_el);
     const double T = row[kPopT];
     const int e = sp_el[sp], st = sp_stage[sp];
-    const double m = el[e] * kAMU;
+    const double m = el[e * kElStride + kElMass] * kAMU;
     const double u = sqrt(2.0 * kKB * T / m + vturb * vturb);
-    const double NU = row[kPopHdr + 2 * e + st];
+    const double NU = row[pop_nu(e, st)];
     const double pre = sqrt(kPI) * kE * kE / (kME * kC);
     SpConst o;
     if (pop32)   // precision-study variant: the population table rounded to FP32 first
@@ -129,8 +129,11 @@ __global__ void k_kappa0(int64_t L, const int* __restrict__ species, const float
 }
 
 // ---------------------------------------------------------------------------
-// k_median: lower median (rank (L-1)/2) of ln kappa0 per row by 4-pass MSB radix
-// selection on order-preserving keys of the FP32 bit patterns.
+// Lower median (rank (L-1)/2) of ln kappa0 per row: MSB radix selection on order-preserving
+// keys of the FP32 bit patterns in three levels of 11, 11 and 10 bits.  At every level a grid
+// of CTAs per row histograms its share of the row (the values whose key matches the prefix
+// resolved so far) in shared memory and adds the non-empty bins to the row's global
+// histogram; one CTA per row then finds the bin holding the rank (k_med_pick).
 __device__ __forceinline__ unsigned fkey(float x) {
     unsigned b = __float_as_uint(x);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -139,44 +142,86 @@ __device__ __forceinline__ float unkey(unsigned k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__global__ void __launch_bounds__(1024) k_median(int64_t L, const float* __restrict__ lnk0, float ln_kc_factor,
-                                                 float ln_cut, float* __restrict__ ln_tp, float* __restrict__ kc_out) {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned s_prefix, s_rank;
-    const int s = blockIdx.x;
+struct MedState {
+    unsigned prefix;   // key bits resolved so far
+    unsigned rank;     // rank of the median among the keys with that prefix
+};
+constexpr int kMedBins = 2048;
+__host__ __device__ constexpr int med_shift(int level) { return level == 0 ? 21 : (level == 1 ? 10 : 0); }
+__host__ __device__ constexpr int med_bits(int level) { return level == 2 ? 10 : 11; }
+
+__global__ void k_med_init(int n_sel, int64_t L, MedState* __restrict__ st, unsigned* __restrict__ ghist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_sel * kMedBins) ghist[i] = 0u;
+    if (i < n_sel) st[i] = MedState{0u, (unsigned)((L - 1) / 2)};
+}
+
+__global__ void __launch_bounds__(1024) k_med_hist(int64_t L, const float* __restrict__ lnk0, int level,
+                                                   const MedState* __restrict__ st, unsigned* __restrict__ ghist) {
+    __shared__ unsigned h[kMedBins];
+    const int s = blockIdx.y;
+    const int shift = med_shift(level), nbits = med_bits(level);
+    const unsigned pmask = level == 0 ? 0u : (0xffffffffu << (shift + nbits));
+    const unsigned prefix = st[s].prefix;
+    for (int i = threadIdx.x; i < kMedBins; i += blockDim.x) h[i] = 0u;
+    __syncthreads();
     const float* x = lnk0 + (size_t)s * L;
-    if (threadIdx.x == 0) {
-        s_prefix = 0;
-        s_rank = (unsigned)((L - 1) / 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += stride) {
+        const unsigned k = fkey(__ldg(x + i));
+        if ((k & pmask) == prefix) atomicAdd(&h[(k >> shift) & ((1u << nbits) - 1u)], 1u);
     }
-    for (int level = 0; level < 4; ++level) {
-        const int shift = 24 - 8 * level;
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
-        __syncthreads();
-        const unsigned prefix = s_prefix;
-        const unsigned pmask = level == 0 ? 0u : (0xffffffffu << (32 - 8 * level));
-        for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
-            unsigned k = fkey(x[i]);
-            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (1 << nbits); i += blockDim.x)
+        if (h[i]) atomicAdd(&ghist[(size_t)s * kMedBins + i], h[i]);
+}
+
+__global__ void __launch_bounds__(1024) k_med_pick(int level, MedState* __restrict__ st,
+                                                   unsigned* __restrict__ ghist, float ln_kc_factor, float ln_cut,
+                                                   float* __restrict__ ln_tp, float* __restrict__ kc_out) {
+    __shared__ int wsum[32];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned* h = ghist + (size_t)s * kMedBins;
+    const int nb = 1 << med_bits(level);
+    // two bins per thread; block-wide inclusive scan of their counts
+    const unsigned c0 = 2 * tid < nb ? h[2 * tid] : 0u, c1 = 2 * tid + 1 < nb ? h[2 * tid + 1] : 0u;
+    const int v = (int)(c0 + c1);
+    int incl = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        int ti = t;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, ti, d);
+            if (lane >= d) ti += y;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned rank = s_rank, acc = 0;
-            int b = 0;
-            for (; b < 255; ++b) {
-                if (acc + hist[b] > rank) break;
-                acc += hist[b];
-            }
-            s_rank = rank - acc;
-            s_prefix = prefix | ((unsigned)b << shift);
+        wsum[lane] = ti - t;
+    }
+    __syncthreads();
+    const unsigned before = (unsigned)(wsum[warp] + incl - v);
+    const MedState cur = st[s];
+    if (cur.rank >= before && cur.rank < before + (unsigned)v) {
+        const bool lo = cur.rank < before + c0;
+        const unsigned bin = 2u * tid + (lo ? 0u : 1u);
+        MedState nx;
+        nx.rank = cur.rank - (lo ? before : before + c0);
+        nx.prefix = cur.prefix | (bin << med_shift(level));
+        st[s] = nx;
+        if (level == 2) {
+            const float med = unkey(nx.prefix);
+            ln_tp[s] = med + ln_kc_factor + ln_cut;
+            if (kc_out) kc_out[s] = expf(med + ln_kc_factor);
         }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const float med = unkey(s_prefix);
-        ln_tp[s] = med + ln_kc_factor + ln_cut;
-        if (kc_out) kc_out[s] = expf(med + ln_kc_factor);
-    }
+    __syncthreads();
+    // clear the histogram for the next level
+    if (2 * tid < kMedBins) h[2 * tid] = 0u;
+    if (2 * tid + 1 < kMedBins) h[2 * tid + 1] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -368,42 +413,68 @@ __global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const
     if (threadIdx.x < kNumClasses) o.blkcnt[((size_t)s * kNumClasses + threadIdx.x) * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// k_scan: per row, exclusive scan of the per-block class counts (one warp per class),
-// class base offsets, and the total number of profile evaluations.
-__global__ void k_scan(int nb, int* __restrict__ blkcnt, int* __restrict__ classbase, int* __restrict__ classcnt,
-                       const long long* __restrict__ wpart, long long* __restrict__ evals) {
-    __shared__ int tot[kNumClasses];
-    const int s = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = warp; b < kNumClasses; b += blockDim.x >> 5) {
-        int* row = blkcnt + ((size_t)s * kNumClasses + b) * nb;
-        int run = 0;
-        for (int base = 0; base < nb; base += 32) {
-            const int k = base + lane;
-            int v = k < nb ? row[k] : 0, incl = v;
-            for (int d = 1; d < 32; d <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += y;
-            }
-            if (k < nb) row[k] = run + incl - v;
-            run += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) tot[b] = run;
-    }
+// k_scan_class: per (class, row), exclusive scan in place of the per-block counts of the
+// class (one CTA each) and the class total.
+__global__ void __launch_bounds__(1024) k_scan_class(int nb, int* __restrict__ blkcnt, int* __restrict__ classcnt) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int b = blockIdx.x, s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int* row = blkcnt + ((size_t)s * kNumClasses + b) * nb;
+    if (tid == 0) carry = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int k = base + tid;
+        const int v = k < nb ? row[k] : 0;
+        int incl = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            int ti = t;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ti, d);
+                if (lane >= d) ti += y;
+            }
+            wsum[lane] = ti - t;
+        }
+        __syncthreads();
+        const int c0 = carry;
+        const int ex = c0 + wsum[warp] + incl - v;
+        if (k < nb) row[k] = ex;
+        __syncthreads();
+        if (tid == (int)blockDim.x - 1) carry = ex + v;
+        __syncthreads();
+    }
+    if (tid == 0) classcnt[s * kNumClasses + b] = carry;
+}
+
+// k_scan_fin: per row, the class base offsets and the total number of profile evaluations.
+__global__ void __launch_bounds__(1024) k_scan_fin(int nb, const int* __restrict__ classcnt,
+                                                   int* __restrict__ classbase, const long long* __restrict__ wpart,
+                                                   long long* __restrict__ evals) {
+    __shared__ long long wsum[32];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
         int acc = 0;
         for (int b = 0; b < kNumClasses; ++b) {
             classbase[s * kNumClasses + b] = acc;
-            classcnt[s * kNumClasses + b] = tot[b];
-            acc += tot[b];
+            acc += classcnt[s * kNumClasses + b];
         }
     }
-    if (evals && warp == 0) {
-        long long acc = 0;
-        for (int k = lane; k < nb; k += 32) acc += wpart[(size_t)s * nb + k];
-        for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-        if (lane == 0) evals[s] = acc;
+    if (!evals) return;
+    long long acc = 0;
+    for (int k = tid; k < nb; k += blockDim.x) acc += wpart[(size_t)s * nb + k];
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        evals[s] = t;
     }
 }
 
@@ -639,10 +710,11 @@ __device__ __forceinline__ void near_line(const NearRec& r, int seg0, bool serie
     }
 }
 
-// One tile of one row.  Called by the grid kernel (one tile per CTA) and by the
-// persistent kernel (a loop over a work list).
+// One tile of one row.  Called by the grid kernel (one tile per CTA, or S CTAs per tile that
+// take every S-th chunk of the tile's candidate lines, sp = 0..S-1, when a call has too few
+// tiles to fill the GPU) and by the persistent kernel (a loop over a work list).
 template <int PREC, int PTS, int THREADS>
-__device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
+__device__ __forceinline__ void tile_body(const RowDesc& g, int tile, int sp = 0, int S = 1) {
     constexpr int TILE = PTS * THREADS;
     __shared__ float4 sFarA[THREADS];
     __shared__ float4 sFarB[THREADS];
@@ -669,6 +741,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
         part[k] = 0.f;
     }
 
+    int chunk = 0;   // running chunk index over the classes: this CTA takes chunk % S == sp
     for (int b = 0; b < kNumClasses; ++b) {
         const int reach = 1 << b;
         int tlo = floordiv(J0 - reach + 1, TILE), thi = floordiv(J0 + TILE - 1 + reach - 1, TILE);
@@ -678,6 +751,7 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile) {
         const int* cum = g.cum + (size_t)b * (g.nT + 3);
         const int beg = cum[tlo + 1], end = cum[thi + 2];
         for (int base = beg; base < end; base += THREADS) {
+            if (chunk++ % S != sp) continue;   // CTA-uniform
             // ---- set-up: one candidate line per thread
             const int pos = base + tid;
             bool isFar = false, isNear = false;
@@ -903,6 +977,8 @@ struct TileArgs {
     const int* ihi;
     const float* ln_tp;
     float* out;
+    int split;       // CTAs per tile (1: direct output)
+    float* part;     // split > 1: partial sums [n_sel][split][N], added by k_split_sum
 };
 
 __device__ __forceinline__ RowDesc row_desc(const TileArgs& g, int s, int tile) {
@@ -935,10 +1011,28 @@ __device__ __forceinline__ RowDesc row_desc(const TileArgs& g, int s, int tile) 
 #ifndef MPSA_TILES_MINB
 #define MPSA_TILES_MINB 4
 #endif
-template <int PREC>
+// SPLIT: g.split CTAs per tile, each writing its partial sums to g.part (a separate
+// instantiation, so that the one-CTA-per-tile form compiles as it would without it)
+template <int PREC, bool SPLIT>
 __global__ void __launch_bounds__(kTileThreads, MPSA_TILES_MINB) k_tiles(TileArgs g) {
-    const RowDesc r = row_desc(g, blockIdx.y, kTile);
-    tile_body<PREC, kPtsPerThread, kTileThreads>(r, blockIdx.x);
+    RowDesc r = row_desc(g, blockIdx.y, kTile);
+    if (SPLIT) {
+        const int sp = blockIdx.x % g.split;
+        r.out = g.part + ((size_t)blockIdx.y * g.split + sp) * g.N;
+        tile_body<PREC, kPtsPerThread, kTileThreads>(r, blockIdx.x / g.split, sp, g.split);
+    } else {
+        tile_body<PREC, kPtsPerThread, kTileThreads>(r, blockIdx.x);
+    }
+}
+
+// kappa[s][j] = sum over the split CTAs' partial sums (FP64 sum, one rounding to FP32)
+__global__ void k_split_sum(int n_sel, int N, int split, const float* __restrict__ part, float* __restrict__ kappa) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_sel * N) return;
+    const int s = (int)(t / N), j = (int)(t % N);
+    double acc = 0.0;
+    for (int q = 0; q < split; ++q) acc += part[((size_t)s * split + q) * N + j];
+    kappa[t] = (float)acc;
 }
 
 // Persistent form: a fixed grid of CTAs pulls (row, tile) units from a work list
@@ -973,7 +1067,7 @@ struct Tile64Args {
     int n_sp;
     const int* sp_el;
     const int* sp_stage;
-    const double* el;          // [5][n_el]
+    const double* el;          // [n_el][kElStride] element records
     int n_el;
     double vturb;
     const double* lam_nm;      // line list
@@ -1026,11 +1120,11 @@ __global__ void __launch_bounds__(256) k_tiles64(Tile64Args g) {
                     const int e = g.sp_el[sp], st = g.sp_stage[sp];
                     const double lam = g.lam_nm[q] * 1e-7;
                     const double nu0 = kC / lam;
-                    const double u = sqrt(2.0 * kKB * T / (g.el[e] * kAMU) + g.vturb * g.vturb);
+                    const double u = sqrt(2.0 * kKB * T / (g.el[e * kElStride + kElMass] * kAMU) + g.vturb * g.vturb);
                     const double dnu = nu0 * u / kC;
                     const double gam = pow(10.0, (double)g.lgR[q]) + pow(10.0, (double)g.lgS[q]) * ne +
                                        pow(10.0, (double)g.lgW[q]) * nHI;
-                    const double NU = row[kPopHdr + 2 * e + st];
+                    const double NU = row[pop_nu(e, st)];
                     const double S = pre * pow(10.0, (double)g.loggf[q]) * NU / (rho * dnu) *
                                      exp(-(double)g.E[q] * kEV / (kKB * T)) * (-expm1(-kH * nu0 / (kKB * T)));
                     const int slot = atomicAdd(&sN, 1);
@@ -1097,6 +1191,8 @@ struct PrepBufs {
     RowConst* rc = nullptr;
     SpConst* spc = nullptr;
     long long* wpart = nullptr;
+    MedState* med = nullptr;
+    unsigned* ghist = nullptr;
     PrepOut po{};
 };
 
@@ -1121,7 +1217,8 @@ int prep_alloc(PrepBufs& b, const mpsa_ctx* ctx, int n_sel, int N, double R, int
         (r = al(&b.blkcnt, (size_t)n_sel * kNumClasses * b.nb)) || (r = al(&b.wpart, (size_t)n_sel * b.nb)) ||
         (r = al(&b.classbase, (size_t)n_sel * kNumClasses)) || (r = al(&b.classcnt, (size_t)n_sel * kNumClasses)) ||
         (r = al(&b.bidx, SL)) || (r = al(&b.bkey, SL)) || (r = al(&b.rec, SL)) ||
-        (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))))
+        (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))) || (r = al(&b.med, n_sel)) ||
+        (r = al(&b.ghist, (size_t)n_sel * kMedBins)))
         return r;
     b.po.blkcnt = b.blkcnt;
     b.po.wpart = b.wpart;
@@ -1145,10 +1242,20 @@ int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const
                                                            ctx->d_el, pop, ctx->vturb, pop32, b.rc, b.spc);
     k_kappa0<<<dim3(lb, n_sel), 256, 0, st>>>(L, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS,
                                                ctx->d_lgW, b.lamcm, n_sp, b.rc, b.spc, b.lnS, b.av, b.lnk0);
-    k_median<<<n_sel, 1024, 0, st>>>(L, b.lnk0, (float)log(kcf), (float)log(cut), b.ln_tp, kc_out);
+    {
+        // median of ln kappa0 per row: three radix levels, each a multi-CTA histogram and a pick
+        const int per_row = (int)std::max<int64_t>(1, std::min<int64_t>(128, (L + 8191) / 8192));
+        k_med_init<<<(n_sel * kMedBins + 255) / 256, 256, 0, st>>>(n_sel, L, b.med, b.ghist);
+        for (int level = 0; level < 3; ++level) {
+            k_med_hist<<<dim3(per_row, n_sel), 1024, 0, st>>>(L, b.lnk0, level, b.med, b.ghist);
+            k_med_pick<<<n_sel, 1024, 0, st>>>(level, b.med, b.ghist, (float)log(kcf), (float)log(cut), b.ln_tp,
+                                               kc_out);
+        }
+    }
     k_prep<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc, b.lnS, b.av,
                                               b.lnk0, b.ln_tp, b.nb, b.po);
-    k_scan<<<n_sel, 32 * 8, 0, st>>>(b.nb, b.blkcnt, b.classbase, b.classcnt, b.wpart, (long long*)evals);
+    k_scan_class<<<dim3(kNumClasses, n_sel), 1024, 0, st>>>(b.nb, b.blkcnt, b.classcnt);
+    k_scan_fin<<<n_sel, 1024, 0, st>>>(b.nb, b.classcnt, b.classbase, b.wpart, (long long*)evals);
     k_scatter<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx, b.bkey,
                                                  b.po, b.rec);
     return ranges_launch(b, b.tile, b.cum, st);
@@ -1186,6 +1293,8 @@ TileArgs tile_args(const PrepBufs& b, float* kappa) {
     ta.ihi = b.po.ihi;
     ta.ln_tp = b.ln_tp;
     ta.out = kappa;
+    ta.split = 1;
+    ta.part = nullptr;
     return ta;
 }
 
@@ -1195,7 +1304,7 @@ int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, do
     if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE && prec != MPSA_PREC_FP64 &&
         prec != MPSA_PREC_FP32_POP32)
         return fail(MPSA_EINVAL, "synth: precision %d", prec);
-    Scratch sc(st);
+    Scratch sc(st, ctx->pool);
     PrepBufs b;
     int r;
     const int tile = prec == MPSA_PREC_FP64 ? kTile64 : kTile;
@@ -1225,10 +1334,44 @@ int synth_rows(mpsa_ctx* ctx, const double* pop, int n_sel, const int* d_sel, do
         g.lam0_nm = lam0_nm;
         g.lnq64 = b.lnq;
         k_tiles64<<<dim3(b.nT, n_sel), 256, 0, st>>>(g);
-    } else if (prec == MPSA_PREC_FP32_NAIVE) k_tiles<MPSA_PREC_FP32_NAIVE><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
-    else k_tiles<MPSA_PREC_FP32_COMPENSATED><<<dim3(b.nT, n_sel), kTileThreads, 0, st>>>(ta);
+    } else {
+        // a call with fewer tiles than two waves of the GPU (narrow windows) splits each tile's
+        // candidate lines over several CTAs, up to 64, and adds their partial sums afterwards
+        int dev = 0, sms = 0;
+        MPSA_CUDA_TRY(cudaGetDevice(&dev));
+        MPSA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t ctas = (int64_t)b.nT * n_sel, want = 2ll * sms * MPSA_TILES_MINB;
+        TileArgs tb = ta;
+        tb.split = ctas >= want ? 1 : (int)std::min<int64_t>(64, (want + ctas - 1) / ctas);
+        tb.part = nullptr;
+        if (tb.split > 1 && (r = sc.alloc(&tb.part, (size_t)n_sel * tb.split * N))) return r;
+        const dim3 grid((unsigned)(b.nT * tb.split), n_sel);
+        const bool naive = prec == MPSA_PREC_FP32_NAIVE;
+        if (tb.split > 1) {
+            if (naive) k_tiles<MPSA_PREC_FP32_NAIVE, true><<<grid, kTileThreads, 0, st>>>(tb);
+            else k_tiles<MPSA_PREC_FP32_COMPENSATED, true><<<grid, kTileThreads, 0, st>>>(tb);
+        } else {
+            if (naive) k_tiles<MPSA_PREC_FP32_NAIVE, false><<<grid, kTileThreads, 0, st>>>(tb);
+            else k_tiles<MPSA_PREC_FP32_COMPENSATED, false><<<grid, kTileThreads, 0, st>>>(tb);
+        }
+        if (tb.split > 1) {
+            const int64_t tot = (int64_t)n_sel * N;
+            k_split_sum<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_sel, N, tb.split, tb.part, kappa);
+        }
+    }
     prof_mark(ctx, MPSA_KERNEL_PROFILE, st);
     MPSA_CUDA_TRY(cudaGetLastError());
+    return MPSA_OK;
+}
+
+int check_species(const mpsa_ctx* ctx, const char* who) {
+    for (int i = 0; i < ctx->n_sp; ++i) {
+        const int e = ctx->h_sp_el[i], st = ctx->h_sp_stage[i];
+        if (e >= ctx->n_el) return fail(MPSA_EINVAL, "%s: species %d refers to element %d of %d", who, i, e, ctx->n_el);
+        if (st >= (int)ctx->h_el[(size_t)e * kElStride + kElStages])
+            return fail(MPSA_EINVAL, "%s: species %d is stage %d of element %d, which has %d stages", who, i, st, e,
+                        (int)ctx->h_el[(size_t)e * kElStride + kElStages]);
+    }
     return MPSA_OK;
 }
 
@@ -1251,13 +1394,11 @@ extern "C" int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_se
     if (ctx->L < 1 || ctx->n_sp < 1) return fail(MPSA_ESTATE, "synth_opacity: no line list loaded");
     if (!ctx->d_pop) return fail(MPSA_ESTATE, "synth_opacity: no atmosphere grid set");
     if (n_sel < 1) return fail(MPSA_EINVAL, "synth_opacity: n_sel = %d", n_sel);
-    for (int i = 0; i < ctx->n_sp; ++i)
-        if (ctx->h_sp_el[i] >= ctx->n_el)
-            return fail(MPSA_EINVAL, "synth_opacity: species %d refers to element %d of %d", i, ctx->h_sp_el[i], ctx->n_el);
+    int N, r;
+    if ((r = check_species(ctx, "synth_opacity"))) return r;
     const int rows = ctx->n_comp * ctx->n_points;
     for (int i = 0; i < n_sel; ++i)
         if (sel[i] < 0 || sel[i] >= rows) return fail(MPSA_EINVAL, "synth_opacity: sel[%d] = %d of %d rows", i, sel[i], rows);
-    int N, r;
     if ((r = check_grid(grid, &N))) return r;
     if ((size_t)n_sel * ctx->L >= (size_t)1 << 31)
         return fail(MPSA_EINVAL, "synth_opacity: n_sel * n_lines must stay below 2^31 (split the rows)");
@@ -1265,7 +1406,7 @@ extern "C" int synth_opacity(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_se
     cudaStream_t st = (cudaStream_t)stream;
     int* d_sel;
     {
-        Scratch s2(st);
+        Scratch s2(st, ctx->pool);
         if ((r = s2.alloc(&d_sel, n_sel))) return r;
         MPSA_CUDA_TRY(cudaMemcpyAsync(d_sel, sel, n_sel * sizeof(int), cudaMemcpyHostToDevice, st));
         r = synth_rows(ctx, ctx->d_pop, n_sel, d_sel, grid->lambda0_nm, grid->R, N, kappa_out, kappa_c_out, evals_out,
@@ -1597,8 +1738,8 @@ int mpsa_batch_create(mpsa_ctx* ctx, int32_t n_groups, const mpsa_batch_group* g
                       int32_t autotune, void* stream, mpsa_batch** out) {
     if (!ctx || !groups || !out || n_groups < 1) return fail(MPSA_EINVAL, "mpsa_batch_create: bad argument");
     if (ctx->L < 1 || !ctx->d_pop) return fail(MPSA_ESTATE, "mpsa_batch_create: load a line list and a grid first");
-    for (int i = 0; i < ctx->n_sp; ++i)
-        if (ctx->h_sp_el[i] >= ctx->n_el) return fail(MPSA_EINVAL, "mpsa_batch_create: species/element mismatch");
+    int rs;
+    if ((rs = check_species(ctx, "mpsa_batch_create"))) return rs;
     const int prec = opts ? opts->precision : 0;
     if (prec != MPSA_PREC_FP32_COMPENSATED && prec != MPSA_PREC_FP32_NAIVE)
         return fail(MPSA_EINVAL, "mpsa_batch_create: precision %d", prec);

@@ -17,7 +17,8 @@ PAIRS = {
     "mpsa_elements": ("Elements", ["n_elements", "mass_amu", "chi_eV", "U1", "U2", "log_eps"]),
     "mpsa_lines": ("Lines", ["n_lines", "lambda_nm", "log_gf", "E_eV", "species", "log_gR", "log_gS", "log_gW"]),
     "mpsa_lgrid": ("LGrid", ["lambda0_nm", "lambda1_nm", "R"]),
-    "mpsa_synth_opts": ("SynthOpts", ["cut", "kc_factor", "precision", "tile"]),
+    "mpsa_synth_opts": ("SynthOpts", ["cut", "kc_factor", "precision", "tile", "continuum", "reserved"]),
+    "mpsa_eos": ("Eos", ["n_elements", "mass_amu", "log_eps", "n_stages", "chi_eV", "lnU"]),
     "mpsa_atmos": ("Atmos", ["n_depth", "m", "T", "P", "comp"]),
     "mpsa_odf_table": ("OdfTable", ["nT", "nP", "log10_T", "log10_P", "K", "n_steps", "odf", "kappa_c", "lam_c_nm",
                                     "widths"]),

@@ -147,3 +147,94 @@ def test_pressure_broadening_perturbers():
     assert abs(tS.gamma[0] / (1e-2 * pop.n_e) - 1) < 1e-6
     assert abs(tW.gamma[0] / (1e-2 * pop.n_HI) - 1) < 1e-6
     assert abs(tS.a[0] * 4 * math.pi * tS.dnuD[0] / tS.gamma[0] - 1) < 1e-14
+
+
+# ---- multi-stage equation of state (App. A): Newton-Raphson on the neutral and electron densities
+
+def two_stage_table(el):
+    # the reduced element table as a two-stage table with constant partition functions
+    n = el.n
+    chi = np.zeros((n, 4)); chi[:, 0] = el.chi_eV
+    lnU = np.zeros((n, 5, 3)); lnU[:, 0, 0] = np.log(el.U1); lnU[:, 1, 0] = np.log(el.U2)
+    return wl.EosTable(el.symbol, el.mass_amu, el.log_eps, np.full(n, 2, dtype=np.int32), chi, lnU)
+
+
+def test_eos_two_stages_equal_the_single_ionisation_balance():
+    # stages I-II with fixed U: the Newton solution equals the bisection of the single-ionisation
+    # charge balance (itself pinned by the pure-hydrogen closed form above)
+    el = wl.elements(15)
+    tab = two_stage_table(el)
+    rng = np.random.default_rng(3)
+    for T, P in zip(np.exp(rng.uniform(math.log(2000), math.log(2e5), 25)), 10 ** rng.uniform(-4, 8, 25)):
+        ab = np.exp(rng.uniform(-4, 2, el.n))
+        a, b = ph.populations(T, P, el, ab), ph.populations_eos(T, P, tab, ab)
+        assert abs(b.n_e / a.n_e - 1) < 1e-11, (T, P)
+        assert np.allclose(b.NU[:, :2], a.NU, rtol=1e-10, atol=0)
+        assert abs(b.rho / a.rho - 1) < 1e-12 and abs(b.n_HI / a.n_HI - 1) < 1e-10
+
+
+def test_eos_pure_hydrogen_closed_form():
+    el = hydrogen_only()
+    tab = two_stage_table(el)
+    k = 1.380649e-16
+    for T in [3000.0, 9000.0, 50000.0]:
+        for P in [1e-2, 1e4, 1e7]:
+            phi = (2 * math.pi * 9.1093837015e-28 * k * T / 6.62607015e-27 ** 2) ** 1.5 \
+                * math.exp(-13.598 * 1.602176634e-12 / (k * T))
+            x = math.sqrt(phi * k * T / (P + phi * k * T))
+            pop = ph.populations_eos(T, P, tab)
+            assert abs(pop.n_e / pop.n_nuc / x - 1) < 1e-11, (T, P)
+
+
+def test_eos_helium_three_stages_cubic():
+    # pure helium with stages I-III and fixed U: with y = n_e / n_tot, a = Phi_0 / n_tot and
+    # b = Phi_1 / n_tot, charge and particle conservation give y^3 + 2a y^2 + (3ab - a) y - 2ab = 0,
+    # whose single positive root (one sign change) comes from numpy.roots
+    tab = wl.EosTable(["He"], np.array([4.0026]), np.array([12.0]), np.array([3], dtype=np.int32),
+                      np.array([[24.587, 54.418, 0.0, 0.0]]), np.zeros((1, 5, 3)))
+    tab.lnU[0, :3, 0] = np.log([1.0, 2.0, 1.0])
+    k, eV = 1.380649e-16, 1.602176634e-12
+    for T in [8000.0, 20000.0, 40000.0, 100000.0]:
+        for P in [1e-2, 1e2, 1e6]:
+            s = (2 * math.pi * 9.1093837015e-28 * k * T / 6.62607015e-27 ** 2) ** 1.5
+            n_tot = P / (k * T)
+            a = 2 * 2.0 / 1.0 * s * math.exp(-24.587 * eV / (k * T)) / n_tot
+            b = 2 * 1.0 / 2.0 * s * math.exp(-54.418 * eV / (k * T)) / n_tot
+            r = np.roots([1.0, 2 * a, 3 * a * b - a, -2 * a * b])
+            y = float(max(z.real for z in r if abs(z.imag) < 1e-12 * abs(z) and z.real > 0))
+            pop = ph.populations_eos(T, P, tab)
+            assert abs(pop.n_e / n_tot / y - 1) < 1e-8, (T, P, pop.n_e / n_tot, y)
+
+
+def test_eos_saha_ratios_and_conservation():
+    # temperature-dependent partition functions, stages up to V: every adjacent pair of stages
+    # satisfies the Saha-Boltzmann ratio, and charge, particles and each element's nuclei are conserved
+    tab = wl.eos_table(15)
+    rng = np.random.default_rng(7)
+    k, eV = ph.K_BOLTZ, ph.EV
+    for T, P in zip(np.exp(rng.uniform(math.log(2000), math.log(2e5), 30)), 10 ** rng.uniform(-4, 8, 30)):
+        ab = np.exp(rng.uniform(-3, 1, tab.n))
+        pop = ph.populations_eos(T, P, tab, ab)
+        U = ph.partition_functions(tab, T)
+        s = (2 * math.pi * ph.M_ELECTRON * k * T / ph.H_PLANCK ** 2) ** 1.5
+        for e in range(tab.n):
+            for j in range(tab.n_stages[e] - 1):
+                lo, hi = pop.n_stage[e, j], pop.n_stage[e, j + 1]
+                if lo > 1e-280 and hi > 1e-280:
+                    phi = 2 * U[e, j + 1] / U[e, j] * s * math.exp(-tab.chi_eV[e, j] * eV / (k * T))
+                    assert abs(hi * pop.n_e / lo / phi - 1) < 1e-10, (T, P, e, j)
+        q = (pop.n_stage * np.arange(5)[None, :]).sum()
+        assert abs(q / pop.n_e - 1) < 1e-12
+        assert abs((pop.n_nuc + pop.n_e) * k * T / P - 1) < 1e-12
+        eps = 10.0 ** (tab.log_eps - 12.0) * ab
+        assert np.allclose(pop.n_stage.sum(axis=1), eps / eps.sum() * pop.n_nuc, rtol=1e-12, atol=0)
+        assert np.all(pop.n_stage >= 0) and np.all(pop.n_stage[np.arange(5)[None, :] >= tab.n_stages[:, None]] == 0)
+
+
+def test_eos_partition_function_at_reference_temperature():
+    # x = ln(T / 5040 K) vanishes at 5040 K: U_j = exp(c0) there; U grows with T where c1, c2 >= 0
+    tab = wl.eos_table(15)
+    U = ph.partition_functions(tab, 5040.0)
+    for e in range(tab.n):
+        assert np.allclose(U[e, :tab.n_stages[e]], np.exp(tab.lnU[e, :tab.n_stages[e], 0]), rtol=1e-15)
+    assert np.all(ph.partition_functions(tab, 20000.0) >= U)

@@ -47,6 +47,19 @@ ELEMENTS = [
     ("Ba", 137.327, 5.212, 1.3, 3.0, 2.18),
 ]
 
+# Ionisation energies [eV] beyond the first (II -> III, III -> IV, IV -> V), approximate
+# standard values used as the synthetic stand-in for the multi-stage equation of state:
+# H has stages I-II, He I-III, every metal I-V (App. E of the paper: N_j/U_j up to j = 5).
+IONISATION_HIGHER = {
+    "H": (), "He": (54.418,), "Fe": (16.199, 30.651, 54.91), "Ca": (11.872, 50.913, 67.27),
+    "Mg": (15.035, 80.144, 109.27), "Si": (16.346, 33.493, 45.142), "Ti": (13.576, 27.492, 43.268),
+    "Na": (47.286, 71.62, 98.94), "Al": (18.829, 28.448, 119.99), "Cr": (16.486, 30.96, 49.16),
+    "Ni": (18.169, 35.19, 54.9), "Mn": (15.64, 33.668, 51.2), "Co": (17.084, 33.5, 51.3),
+    "V": (14.634, 29.311, 46.709), "Sc": (12.8, 24.757, 73.49), "Sr": (11.03, 42.89, 57.0),
+    "Ba": (10.004, 35.84, 47.0),
+}
+MAX_STAGES = 5
+
 # The 12-step sub-bin widths of the DFSYNTHE ODF: nine of 0.1, then 0.05,
 # 0.04, 0.01 (Sect. 2.3 / App. E; the configuration of Castelli 2005).
 ODF_WIDTHS_12 = np.array([0.1] * 9 + [0.05, 0.04, 0.01], dtype=np.float64)
@@ -74,6 +87,61 @@ def elements(n_metals: int) -> Elements:
     rows = ELEMENTS[: 2 + n_metals]
     col = lambda i: np.array([r[i] for r in rows], dtype=np.float64)
     return Elements([r[0] for r in rows], col(1), col(2), col(3), col(4), col(5))
+
+
+@dataclass
+class EosTable:
+    """Element data of the multi-stage equation of state (App. A, E of the paper).
+
+    Element e has stages 0 .. n_stages[e]-1 (I, II, ...); chi_eV[e, j] is the ionisation
+    energy from stage j to j + 1; the partition function of stage j is given by
+    ln U_j(T) = lnU[e, j, 0] + lnU[e, j, 1] x + lnU[e, j, 2] x^2 with x = ln(T / 5040 K).
+    Unused entries (stages at or beyond n_stages) are zero."""
+    symbol: list
+    mass_amu: np.ndarray     # [n]
+    log_eps: np.ndarray      # [n]
+    n_stages: np.ndarray     # int32 [n], 1..5
+    chi_eV: np.ndarray       # [n, 4]
+    lnU: np.ndarray          # [n, 5, 3]
+
+    @property
+    def n(self) -> int:
+        return len(self.symbol)
+
+
+def eos_table(n_metals: int, seed: int = 1010) -> EosTable:
+    """H, He and the first ``n_metals`` metals with all their stages up to V (H: I-II, He: I-III).
+
+    The first ionisation energies and the constant terms of stages I and II are those of the
+    element table (partition functions U1, U2 at 5040 K); the constant terms of the higher
+    stages are ground-state weights drawn from {1, ..., 30} and the temperature terms of every
+    stage are drawn as c1 ~ U(0, 0.4), c2 ~ U(0, 0.1) (a seeded synthetic stand-in for fits to
+    tabulated partition functions); H II and He III (bare nuclei) and H I keep constant U."""
+    rng = np.random.default_rng(seed)
+    rows = ELEMENTS[: 2 + n_metals]
+    n = len(rows)
+    ns = np.array([2 if r[0] == "H" else (3 if r[0] == "He" else MAX_STAGES) for r in rows], dtype=np.int32)
+    chi = np.zeros((n, MAX_STAGES - 1))
+    lnU = np.zeros((n, MAX_STAGES, 3))
+    for e, r in enumerate(rows):
+        chi[e, 0] = r[2]
+        chi[e, 1:ns[e] - 1] = IONISATION_HIGHER[r[0]][: ns[e] - 2]
+        g0 = np.r_[r[3], r[4], rng.integers(1, 31, MAX_STAGES - 2)].astype(np.float64)
+        c1 = rng.uniform(0.0, 0.4, MAX_STAGES)
+        c2 = rng.uniform(0.0, 0.1, MAX_STAGES)
+        for j in range(ns[e]):
+            const = (r[0] == "H") or (r[0] == "He" and j == 2)
+            lnU[e, j] = [math.log(g0[j]), 0.0 if const else c1[j], 0.0 if const else c2[j]]
+    col = lambda i: np.array([r[i] for r in rows], dtype=np.float64)
+    return EosTable([r[0] for r in rows], col(1), col(5), ns, chi, lnU)
+
+
+def species_table_eos(n_metals: int, n_stages: int = 3):
+    """Line-bearing species of the metals in stages I .. n_stages: species s maps to element
+    2 + s // n_stages and stage s % n_stages."""
+    el = np.repeat(np.arange(2, 2 + n_metals, dtype=np.int32), n_stages)
+    stage = np.tile(np.arange(n_stages, dtype=np.int32), n_metals)
+    return el, stage
 
 
 def species_table(n_metals: int):
