@@ -43,6 +43,10 @@ UNIT = "line-evals/s"
 # reciprocal on the special-function unit (not counted).
 FLOP_PER_EVAL = 6.5
 FP32_LANES_PER_SM = 128
+# kernels of the library per timed step: synth_opacity (k_place, k_consts, k_kappa0, k_med_init,
+# three k_med_hist + k_med_pick levels, k_prep, k_scan_class, k_scan_fin, k_scatter, k_ranges,
+# k_tiles) and build_odf (k_odf)
+LAUNCHES_PER_STEP = 17
 
 
 def parse():
@@ -61,9 +65,9 @@ def parse():
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
     p.add_argument("--batch-windows", type=int, default=24, help="spectrum windows in the batch sample")
-    p.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window of the request stream")
-    p.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
-    p.add_argument("--serve-limit", type=float, default=90.0, help="wall-clock limit of a serving run [s]")
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the latency stream")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving sub-measurement of the step mode")
+    p.add_argument("--no-batch-leg", action="store_true", help="skip the batch sub-measurement of the step mode")
     p.add_argument("--bin-rays", type=int, default=8192, help="rays per step of the bin-intensity form")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,8 +396,15 @@ def native_arm(args):
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
     achieved = evals_per_launch * FLOP_PER_EVAL / (tiles_avg / 1e3) / 1e12
     traffic = measured_traffic("k_tiles", ["synth.cu", "voigt.cuh", "common.cuh"], sel)
+    counted = profile_value("k_tiles_fp32_ops_row1044.md", "flop_per_eval_counted", "k_tiles",
+                            ["synth.cu", "voigt.cuh", "common.cuh"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_tiles (profile synthesis)",
+                "fp32_counted": None if counted is None else {
+                    "flop_per_eval": counted, "achieved": achieved * counted / FLOP_PER_EVAL,
+                    "frac": achieved * counted / FLOP_PER_EVAL / fp32_peak,
+                    "source": "ncu FP32 thread-instruction counters (FFMA2 x4, FFMA x2, FMUL, FADD) on row 1044, "
+                              "profiles/k_tiles_fp32_ops_row1044.md"},
                 "peak_kind": f"FP32 FMA peak {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz",
                 "sms": sms, "flop_per_eval": FLOP_PER_EVAL, "avg_launch_ms": tiles_avg, "launches": tiles_n}
     odf_avg = odf_ms / max(odf_n, 1)
@@ -402,6 +413,14 @@ def native_arm(args):
                     "frac": odf_bytes / (odf_avg / 1e3) / 1e9 / hbm,
                     "traffic": measured_traffic("k_odf", ["odf.cu", "common.cuh"], sel), "kernel": "k_odf (build_odf)",
                     "peak_kind": f"{peak_kind} HBM copy bandwidth", "avg_launch_ms": odf_avg, "launches": odf_n}
+    ctx.close()
+    # the other parts of the headline metric: the batched form against the plain per-point path,
+    # and continuous batching against one request at a time (throughput, p50 / p99 latency)
+    batch = serving = None
+    if world == 1 and args.workload == "table" and not args.no_batch_leg:
+        batch = batch_measure(w, lines, el, se, ss, n_rows=2, n_windows=24, steps=2)
+    if world == 1 and args.workload == "table" and not args.no_serve:
+        serving = serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=args.serve_seconds)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         T0, P0 = float(w.T[sel[0]]), float(w.P[sel[0]])
@@ -420,14 +439,15 @@ def native_arm(args):
                       "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"independent points x{world}"},
            "odf_points_per_s": odf_pts, "evals_per_step": evals / args.steps,
            "roofline": roofline, "roofline_odf": roofline_odf, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": 10 * args.steps, "clocks": clk}
+           "batch": batch, "serving": serving,
+           "gpu_launches": LAUNCHES_PER_STEP * args.steps, "clocks": clk}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
 # ---------------------------------------------------------------------------
-def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
+def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9, n_max=None):
     """Poisson arrivals of mixed requests (the serving workload).
 
     Spectrum: grey atmosphere with D ~ U{40..120} depths, Teff ~ U(3500, 12000) K, log g ~ U(1, 5);
@@ -435,7 +455,7 @@ def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
     ODF: one composition x the 57 x 25 T-P grid over 1-10 contiguous intervals of the 328-interval grid."""
     rng = np.random.default_rng(seed)
     t, out = 0.0, []
-    while True:
+    while n_max is None or len(out) < n_max:
         t += rng.exponential(1.0 / rate)
         if t > seconds:
             break
@@ -453,14 +473,15 @@ def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9):
     return out
 
 
-def serve_arm(args):
-    import torch
-
+def serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=20.0, load=0.7, seed=2024, limit=120.0):
+    """Continuous batching against one request at a time, on the serving workload's request mix
+    (90 % spectra of 40-120 depths over 1-500 nm windows at R = 5e5, 10 % ODFs of one composition
+    over the 57 x 25 grid on 1-10 intervals).
+      saturation: the same n_burst requests (the mix's proportions: 10 % ODFs) submitted at once;
+        completed requests per second with 8 stream slots and with 1;
+      latency: a Poisson stream offered at `load` times the one-slot saturation rate for
+        stream_s seconds, served with 8 slots and with 1; p50 / p99 of completion - arrival."""
     from paper_2105_13611_gb300 import binding
-    w = wl.config_table()
-    lines = w.lines()
-    el = wl.elements(w.n_metals)
-    se, ss = wl.species_table(w.n_metals)
     N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
     bounds_full = wl.equal_intervals(N, w.n_intervals)
     lnq = math.log1p(1.0 / w.grid.R)
@@ -475,83 +496,97 @@ def serve_arm(args):
         b = np.minimum(bounds_full[k0:k0 + nint + 1] - j0, n_sub)
         return rows, g, b, w.widths
 
-    def run_stream(stream, max_inflight, limit):
-        ctx = binding.Context(0)
-        ctx.load_linelist(lines, se, ss)
-        ctx.set_atmosphere_grid(el, w.T, w.P)
+    ctx = binding.Context(0)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P)
+
+    def run(stream, max_inflight):
         srv = binding.Server(ctx, hbm_budget_bytes=int(120e9), max_inflight=max_inflight, rows_per_chunk=8)
         t0 = time.perf_counter()
-        pending = []
-        i = 0
-        lat = {"spectrum": [], "odf": []}
+        pending, lat, i = [], {"spectrum": [], "odf": []}, 0
         while time.perf_counter() - t0 < limit:
             now = time.perf_counter() - t0
             while i < len(stream) and stream[i][0] <= now:
                 _, kind, a = stream[i]
                 tk = srv.submit_spectrum(*a[:3], a[3], mus) if kind == "spectrum" else srv.submit_odf(*odf_args(*a))
-                pending.append((tk, kind))
+                pending.append((tk, kind, stream[i][0]))
                 i += 1
             still = []
-            for tk, kind in pending:
+            for tk, kind, t_arr in pending:
                 try:
-                    _, ms = srv.wait(tk, timeout_ms=0)
-                    lat[kind].append(ms)
+                    srv.wait(tk, timeout_ms=0)
+                    lat[kind].append((time.perf_counter() - t0 - t_arr) * 1e3)
                 except binding.MpsaError as e:
-                    if e.code == binding.MPSA_ETIMEOUT:
-                        still.append((tk, kind))
-                    else:
+                    if e.code != binding.MPSA_ETIMEOUT:
                         raise
+                    still.append((tk, kind, t_arr))
             pending = still
             if i >= len(stream) and not pending:
                 break
-            time.sleep(0.002)
+            time.sleep(0.001)
         wall = time.perf_counter() - t0
-        n_cancel = srv.cancel_queued()
+        srv.cancel_queued()
         srv.close()
-        ctx.close()
         done = sum(len(v) for v in lat.values())
-        allv = sorted(lat["spectrum"] + lat["odf"])
+        allv = lat["spectrum"] + lat["odf"]
         pct = lambda v, q: float(np.percentile(v, q)) if v else None
-        return {"offered": len(stream), "submitted": i, "completed": done, "cancelled_unadmitted": n_cancel,
-                "wall_s": wall, "throughput_req_s": done / wall,
+        return {"offered": len(stream), "completed": done, "wall_s": wall, "req_per_s": done / wall,
                 "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
-                "spectrum": {"n": len(lat["spectrum"]), "p50_ms": pct(lat["spectrum"], 50), "p99_ms": pct(lat["spectrum"], 99)},
+                "spectrum": {"n": len(lat["spectrum"]), "p50_ms": pct(lat["spectrum"], 50),
+                             "p99_ms": pct(lat["spectrum"], 99)},
                 "odf": {"n": len(lat["odf"]), "p50_ms": pct(lat["odf"], 50), "p99_ms": pct(lat["odf"], 99)}}
 
-    stream = make_request_stream(args.serve_rate, args.serve_seconds, seed=2024)
-    res = run_stream(stream, 8, args.serve_limit)
-    # the same requests one at a time (no overlap), as many as fit in the same wall-clock limit
-    seq = run_stream(stream, 1, args.serve_limit)
-    out = {"mode": "serve", "metric": "requests/s and latency", "offered_rate_req_s": args.serve_rate,
-           "arrival_window_s": args.serve_seconds, "mix": "90% spectrum (R=5e5 windows) / 10% ODF (57x25 grid)",
-           "continuous_batching": res, "one_at_a_time": seq,
-           "saturated": res["completed"] < res["offered"], "data": "synthetic"}
-    print(json.dumps(out), flush=True)
+    # warm-up: one request of each kind
+    run([(0.0, k, a) for k, a in [r[1:] for r in make_request_stream(50.0, 10.0, seed=seed + 7)][:1]] +
+        [(0.0, "odf", (0, 1))], 1)
+    pool_ = make_request_stream(1e6, 1e6, seed=seed, n_max=40 * n_burst)
+    n_odf = max(1, round(0.1 * n_burst))
+    burst = [r for r in pool_ if r[1] == "odf"][:n_odf] + [r for r in pool_ if r[1] == "spectrum"][:n_burst - n_odf]
+    burst = [(0.0, k, a) for _, k, a in burst]
+    sat8 = run(burst, 8)
+    sat1 = run(burst, 1)
+    rate = load * sat1["req_per_s"]
+    stream = make_request_stream(rate, stream_s, seed=seed + 1)
+    lat8 = run(stream, 8)
+    lat1 = run(stream, 1)
+    ctx.close()
+    return {"mix": "90% spectra (40-120 depths, 1-500 nm at R=5e5, 5 mu) / 10% ODFs (57x25 grid, 1-10 intervals)",
+            "saturation": {"requests": n_burst, "continuous_batching_8_slots": sat8, "one_at_a_time": sat1,
+                           "speedup": sat8["req_per_s"] / sat1["req_per_s"]},
+            "latency": {"offered_req_per_s": rate, "offered_load_vs_one_at_a_time_capacity": load,
+                        "arrival_window_s": stream_s, "continuous_batching_8_slots": lat8, "one_at_a_time": lat1}}
 
 
-def batch_arm(args):
-    """64 compositions x 1425 (T, P) rows plus spectrum windows (1-500 nm at R = 5e5): a seeded
-    sample of ODF rows and windows runs (a) point by point through synth_opacity / build_odf and
-    (b) as one persistent graph-captured batch; same results, compared throughput."""
-    import torch
-
-    from paper_2105_13611_gb300 import binding
+def serve_arm(args):
     w = wl.config_table()
     lines = w.lines()
     el = wl.elements(w.n_metals)
     se, ss = wl.species_table(w.n_metals)
+    out = {"mode": "serve", "metric": "requests/s and latency (continuous batching vs one at a time)",
+           **serve_measure(w, lines, el, se, ss, stream_s=args.serve_seconds), "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+
+
+def batch_measure(w, lines, el, se, ss, n_rows, n_windows, steps, seed=99):
+    """64 compositions x 1425 (T, P) rows plus spectrum windows (1-500 nm at R = 5e5): a seeded
+    sample of n_rows ODF rows and n_windows windows runs (a) point by point through
+    synth_opacity / build_odf and (b) as one persistent graph-captured batch; same results,
+    compared throughput (both timed from the host around `steps` runs, synchronised)."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
     ab = wl.abundance_scales(64, el.n, seed=77)
     ctx = binding.Context(0)
     ctx.load_linelist(lines, se, ss)
     ctx.set_atmosphere_grid(el, w.T, w.P, abund_scale=ab)
     nrows = 64 * len(w.T)
-    rng = np.random.default_rng(99)
+    rng = np.random.default_rng(seed)
     N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
     bounds = wl.equal_intervals(N, w.n_intervals)
     groups = []
-    odf_rows = rng.choice(nrows, args.batch_rows, replace=False).astype(np.int32)
+    odf_rows = rng.choice(nrows, n_rows, replace=False).astype(np.int32)
     groups.append(dict(grid=w.grid, sel=odf_rows, bounds=bounds, widths=w.widths, odf_on=True))
-    for _ in range(args.batch_windows):
+    for _ in range(n_windows):
         L = float(np.exp(rng.uniform(0.0, math.log(500.0))))
         lam0 = float(rng.uniform(9.0, 10000.0 - L))
         groups.append(dict(grid=wl.Grid(lam0, lam0 + L, 5e5), sel=np.array([rng.integers(0, nrows)], dtype=np.int32),
@@ -564,53 +599,56 @@ def batch_arm(args):
         if g["odf_on"]:
             g["odf"] = torch.empty((len(g["sel"]), w.n_intervals, 12), dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
-    # (a) plain per-point path
-    plain_out = []
 
     def plain():
-        outs = []
         for g in groups:
             for i, r in enumerate(g["sel"]):
                 k = g["kappa"][i:i + 1]
                 ctx.synth_opacity(g["grid"], [int(r)], k, g["kappa_c"][i:i + 1], g["evals"][i:i + 1], stream=st)
                 if g["odf_on"]:
                     ctx.build_odf(k, g["bounds"], g["widths"], g["odf"][i:i + 1], stream=st)
-        return outs
 
     plain()
     torch.cuda.synchronize()
     evals = int(sum(int(g["evals"].sum()) for g in groups))
-    ref = [(g["kappa"].clone(), g.get("odf").clone() if g["odf_on"] else None) for g in groups]
+    ref = [g["kappa"].clone() for g in groups]
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         plain()
     torch.cuda.synchronize()
-    t_plain = (time.perf_counter() - t0) / args.steps
-    # (b) batched
+    t_plain = (time.perf_counter() - t0) / steps
     t0 = time.perf_counter()
     batch = binding.Batch(ctx, groups, autotune=True)
     t_create = time.perf_counter() - t0
     batch.run()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
+    t0 = time.perf_counter()
+    for _ in range(steps):
         batch.run(stream=st)
-    e1.record(st)
     torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_batch = (time.perf_counter() - t0) / steps
     worst = 0.0
-    for g, (k_ref, o_ref) in zip(groups, ref):
+    for g, k_ref in zip(groups, ref):
         kb, kr = g["kappa"].double(), k_ref.double()
         kc = g["kappa_c"].double()[:, None]
         worst = max(worst, float(((kb - kr).abs() / (kr + kc)).max()))
     info = batch.info()
     batch.close()
-    out = {"mode": "batch", "metric": "line-evals/s, persistent graph-captured batch vs plain per-point path",
-           "rows": {"odf_rows": len(odf_rows), "windows": args.batch_windows, "compositions": 64},
-           "evals_per_run": evals, "plain_s": t_plain, "batch_s": t_batch,
-           "plain_evals_per_s": evals / t_plain, "batch_evals_per_s": evals / t_batch, "speedup": t_plain / t_batch,
-           "batch_create_s": t_create, "max_rel_diff_vs_plain": worst, "autotune": info, "data": "synthetic"}
+    ctx.close()
+    return {"metric": "line-evals/s, persistent graph-captured batch vs plain per-point path",
+            "rows": {"odf_rows": len(odf_rows), "windows": n_windows, "compositions": 64},
+            "evals_per_run": evals, "plain_s": t_plain, "batch_s": t_batch,
+            "plain_evals_per_s": evals / t_plain, "batch_evals_per_s": evals / t_batch, "speedup": t_plain / t_batch,
+            "batch_create_s": t_create, "max_rel_diff_vs_plain": worst, "autotune": info}
+
+
+def batch_arm(args):
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    out = {"mode": "batch", **batch_measure(w, lines, el, se, ss, args.batch_rows, args.batch_windows, args.steps),
+           "data": "synthetic"}
     print(json.dumps(out), flush=True)
 
 
@@ -701,12 +739,35 @@ def bins_arm(args):
     print(json.dumps(out_line), flush=True)
 
 
+_PREC_STATE = None
+
+
+def _prec_worker_init(path):
+    # the line list, memory-mapped from the arrays the parent saved
+    global _PREC_STATE
+    arrs = {f: np.load(os.path.join(path, f + ".npy"), mmap_mode="r") for f in
+            ("lam_nm", "log_gf", "E_eV", "species", "log_gR", "log_gS", "log_gW")}
+    _PREC_STATE = wl.LineList(**arrs)
+
+
+def _prec_worker(job):
+    from oracle import synthesis as sy
+    r, T, P, js, lam0, lam1, R = job
+    el = wl.elements(15)
+    se, ss = wl.species_table(15)
+    k, sl, kc = sy.kappa_at_chunked(_PREC_STATE, se, ss, el, T, P, wl.Grid(lam0, lam1, R), js)
+    return r, k, sl, kc
+
+
 def precision_arm(args):
     """Precision study: a 1e8-line list (same distributions, 9-10000 nm) on a 6 x 5 (T, P)
     subset of the table, synthesised on a 1 nm slice (300-301 nm at R = 2e6, every line of the
-    list whose cut window reaches it) with the four precisions of the library; relative errors
-    of opacity and ODF steps against the all-FP64 GPU variant (itself checked against the FP64
-    oracle by the GPU tests)."""
+    list whose cut window reaches it) with the four precisions of the library.  Relative errors
+    of the opacity against the FP64 oracle at 24 sampled grid points of every row (the oracle's
+    chunked sampled synthesis over the whole list, in spawned processes: kappa_c from the median
+    over all 1e8 lines), and of opacity and ODF steps against the all-FP64 GPU variant."""
+    import multiprocessing as mp
+    import shutil
     import torch
 
     from paper_2105_13611_gb300 import binding
@@ -738,7 +799,7 @@ def precision_arm(args):
         o = torch.empty((len(rows), 4, 12), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(0, len(rows), 6):  # six rows per call: scratch is ~57 B per (row, line)
+        for i in range(0, len(rows), 6):  # six rows per call: scratch is ~105 B per (row, line)
             ctx.synth_opacity(g, rows[i:i + 6], k[i:i + 6], kc[i:i + 6], ev[i:i + 6],
                               opts=binding.make_opts(1e-3, 1e-2, prec))
         ctx.build_odf(k, b, wl.ODF_WIDTHS_12, o)
@@ -747,80 +808,72 @@ def precision_arm(args):
         print(f"precision: {names[prec]} {times[names[prec]]:.1f} s", file=sys.stderr, flush=True)
         res[prec] = (k.double().cpu().numpy(), kc.double().cpu().numpy(), o.cpu().numpy())
         evals = int(ev.sum())
+    ctx.close()
+    # ---- the FP64 oracle at sampled points of every row
+    rng = np.random.default_rng(5)
+    lnq = math.log1p(1.0 / g.R)
+    i0, i1 = np.searchsorted(lines.lam_nm, [g.lam0_nm, g.lam1_nm])
+    strong = i0 + np.argsort(lines.log_gf[i0:i1])[-8:]
+    centres = np.clip(np.round(np.log(lines.lam_nm[strong] / g.lam0_nm) / lnq).astype(np.int64), 0, N - 1)
+    js = np.unique(np.r_[rng.integers(0, N, 16), centres])
+    tmp = tempfile.mkdtemp(prefix="mpsa_lines_")
+    t0 = time.perf_counter()
+    try:
+        for f in ("lam_nm", "log_gf", "E_eV", "species", "log_gR", "log_gS", "log_gW"):
+            np.save(os.path.join(tmp, f + ".npy"), getattr(lines, f))
+        del lines
+        jobs = [(int(r), float(T[r]), float(P[r]), js, g.lam0_nm, g.lam1_nm, g.R) for r in rows]
+        n_proc = min(len(jobs), max(1, (os.cpu_count() or 1)))
+        with mp.get_context("spawn").Pool(n_proc, initializer=_prec_worker_init, initargs=(tmp,)) as pool:
+            orc = {r: (k_, s_, kc_) for r, k_, s_, kc_ in pool.map(_prec_worker, jobs)}
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    t_orc = time.perf_counter() - t0
+    print(f"precision: oracle at {len(js)} points x {len(rows)} rows in {t_orc:.1f} s", file=sys.stderr, flush=True)
     kr, kcr, orf = res[2]
     out = {"mode": "precision", "lines": n_lines, "rows": "6 T x 5 P of the 57 x 25 grid", "slice_nm": [300.0, 301.0],
-           "grid_points": N, "evals_per_variant": evals, "reference": "fp64_all (GPU)",
+           "grid_points": N, "evals_per_variant": evals, "reference": "FP64 oracle at sampled points; fp64_all (GPU) dense",
+           "oracle_points_per_row": len(js), "oracle_s": t_orc, "oracle_processes": n_proc,
            "generate_s": t_gen, "load_s": t_load, "seconds": times, "variants": {}}
-    for prec in (1, 0, 3):
+    for prec in (2, 1, 0, 3):
         k, kc, o = res[prec]
-        rel = np.abs(k - kr) / (kr + kcr[:, None])
-        ro = np.abs(o - orf) / np.maximum(np.abs(orf), 1e-300)
-        out["variants"][names[prec]] = {"opacity_max_rel": float(rel.max()), "opacity_p99_rel": float(np.quantile(rel, 0.99)),
-                                        "odf_max_rel": float(ro.max()), "odf_p99_rel": float(np.quantile(ro, 0.99))}
+        rel_o, viol, kc_dev = [], 0, 0.0
+        for n, r in enumerate(rows):
+            ko, so, kco = orc[int(r)]
+            kg = k[n, js]
+            rel_o.append(np.abs(kg - ko) / (ko + kco))
+            viol += int(np.sum(np.abs(kg - ko) > 1e-4 * (ko + kco) + so * 1.001))
+            kc_dev = max(kc_dev, abs(kc[n] / kco - 1))
+        rel_o = np.concatenate(rel_o)
+        v = {"opacity_vs_oracle_max_rel": float(rel_o.max()), "opacity_vs_oracle_p99_rel": float(np.quantile(rel_o, 0.99)),
+             "points_beyond_1e-4_tolerance": viol, "points_checked": int(len(rel_o)), "kappa_c_vs_oracle_max_rel": kc_dev}
+        if prec != 2:
+            rel = np.abs(k - kr) / (kr + kcr[:, None])
+            ro = np.abs(o - orf) / np.maximum(np.abs(orf), 1e-300)
+            v.update({"opacity_vs_fp64_gpu_max_rel": float(rel.max()), "opacity_vs_fp64_gpu_p99_rel": float(np.quantile(rel, 0.99)),
+                      "odf_vs_fp64_gpu_max_rel": float(ro.max()), "odf_vs_fp64_gpu_p99_rel": float(np.quantile(ro, 0.99))})
+        out["variants"][names[prec]] = v
     print(json.dumps(out), flush=True)
 
 
-def table_arm(args):
-    """The whole ODF table once: every (T, P) row of the 57 x 25 grid through synth_opacity and
-    build_odf, in chunks of 16 rows, timed with CUDA events per chunk (inputs resident: the
-    line list and the population table).  Prints the wall time, the line-evaluation rate and
-    the ODF (T, P) points per second of the whole table, and the slowest chunks."""
-    import torch
-
-    from paper_2105_13611_gb300 import binding
-    w = wl.config_table()
-    lines = w.lines()
-    el = wl.elements(w.n_metals)
-    se, ss = wl.species_table(w.n_metals)
-    ctx = binding.Context(0)
-    ctx.load_linelist(lines, se, ss)
-    ctx.set_atmosphere_grid(el, w.T, w.P)
-    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
-    K = w.n_intervals
-    bounds = wl.equal_intervals(N, K)
-    chunk = 16
-    rows = np.arange(len(w.T), dtype=np.int32)
-    kap = torch.empty((chunk, N), dtype=torch.float32, device="cuda")
-    kc = torch.empty(chunk, dtype=torch.float32, device="cuda")
-    ev = torch.empty(chunk, dtype=torch.int64, device="cuda")
-    odf = torch.empty((len(rows), K, len(w.widths)), dtype=torch.float64, device="cuda")
-    st = torch.cuda.current_stream()
-    opts = binding.make_opts(w.cut, w.kc_factor)
-    # warm-up on the first chunk
-    ctx.synth_opacity(w.grid, rows[:chunk], kap, kc, ev, opts=opts, stream=st)
-    ctx.build_odf(kap, bounds, w.widths, odf[:chunk], stream=st)
-    torch.cuda.synchronize()
-    clocks = Clocks(0)
-    clocks.start()
-    ctx.profile_enable(True)
-    ctx.profile_read(binding.KERNEL_PROFILE)
-    ctx.profile_read(binding.KERNEL_ODF)
-    evs, per_chunk = 0, []
-    t0 = time.perf_counter()
-    for i in range(0, len(rows), chunk):
-        sel = rows[i:i + chunk]
-        n = len(sel)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        ctx.synth_opacity(w.grid, sel, kap[:n], kc[:n], ev[:n], opts=opts, stream=st)
-        ctx.build_odf(kap[:n], bounds, w.widths, odf[i:i + n], stream=st)
-        e1.record(st)
-        e1.synchronize()
-        per_chunk.append((int(sel[0]), int(sel[-1]), e0.elapsed_time(e1) / 1e3, int(ev[:n].sum())))
-        evs += per_chunk[-1][3]
-    wall = time.perf_counter() - t0
-    tiles_ms, _ = ctx.profile_read(binding.KERNEL_PROFILE)
-    odf_ms, _ = ctx.profile_read(binding.KERNEL_ODF)
-    clk = clocks.stop()
-    gpu_s = sum(c[2] for c in per_chunk)
-    slow = sorted(per_chunk, key=lambda c: -c[2])[:5]
-    out = {"mode": "table", "metric": "whole 57 x 25 ODF table: wall time, line-evals/s, ODF (T,P) points/s",
-           "rows": len(rows), "grid_points": N, "intervals": K, "lines": len(lines), "chunk_rows": chunk,
-           "wall_s": wall, "gpu_s": gpu_s, "evals": evs, "evals_per_s": evs / gpu_s,
-           "odf_points_per_s": len(rows) / gpu_s, "k_tiles_s": tiles_ms / 1e3, "k_odf_s": odf_ms / 1e3,
-           "slowest_chunks": [{"rows": [a, b], "s": t, "evals": e} for a, b, t, e in slow],
-           "clocks": clk, "data": "synthetic"}
-    print(json.dumps(out), flush=True)
+def profile_value(name, key, kernel, sources):
+    """A number recorded in a profiles/ summary (key: value), or None when the summary is missing
+    or was taken on kernel sources that have changed since (SHA-1 of the files)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = hashlib.sha1()
+    for f in sources:
+        with open(os.path.join(ROOT, "paper_2105_13611_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    m_src = re.search(rf"^{kernel}_source_sha1: ([0-9a-f]+)$", text, re.M)
+    m_val = re.search(rf"^{key}: ([0-9.eE+-]+)$", text, re.M)
+    if not (m_src and m_val) or m_src.group(1) != h.hexdigest():
+        return None
+    return float(m_val.group(1))
 
 
 def measured_traffic(kernel, sources, rows):

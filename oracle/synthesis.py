@@ -152,3 +152,52 @@ def kappa_at(pl: PointLines, js, slack_band: float = 3e-5):
         kap[n] = np.sum(e[e >= pl.t])
         sl[n] = np.sum(e[np.abs(e / pl.t - 1.0) <= slack_band])
     return kap, sl
+
+
+def h_upper_bound(v, a):
+    """An upper bound of H(v, a): splitting the convolution integral of H at |t| = |v|/2 gives
+    H <= 4a / (sqrt(pi) v^2) + exp(-v^2 / 4) (and H <= H(0, a) <= 1 always)."""
+    v = np.abs(np.asarray(v, dtype=np.float64))
+    with np.errstate(divide="ignore"):
+        b = 4.0 * a / (math.sqrt(math.pi) * v * v) + np.exp(-v * v / 4.0)
+    return np.minimum(b, 1.0)
+
+
+def kappa_at_chunked(lines, species_el, species_stage, el, T, P, grid, js, cut=1e-3, kc_factor=1e-2,
+                     abund_scale=None, vturb=0.0, slack_band=3e-5, chunk=2_000_000):
+    """kappa_at for line lists too large to prepare at once, in chunks of `chunk` lines: the same
+    steps (populations; the line terms; kappa_c = kc_factor times the lower median of kappa0 over
+    every line of the list, t = cut kappa_c; at each grid index of js the sum of ell over the
+    lines with ell >= t there, and the edge slack).  A line takes part only if S times the upper
+    bound of H at its smallest |v| over the sampled points reaches t (1 - slack_band), which no
+    line that contributes or lies in the slack band can fail.  Returns (kappa, slack, kappa_c)."""
+    js = np.asarray(js, dtype=np.int64)
+    pop = physics.populations_eos(T, P, el, abund_scale) if hasattr(el, "n_stages") else \
+        physics.populations(T, P, el, abund_scale)
+    L = len(lines)
+    lnk0 = np.empty(L)
+    for i in range(0, L, chunk):
+        sub = lines.subset(slice(i, min(i + chunk, L)))
+        t_ = physics.line_terms(sub, species_el, species_stage, el, pop, vturb)
+        lnk0[i:i + len(sub)] = np.log(t_.S * H(0.0, t_.a))
+    kc = kc_factor * float(np.exp(np.partition(lnk0, (L - 1) // 2)[(L - 1) // 2]))
+    del lnk0
+    t = cut * kc
+    thr = (1.0 - slack_band) * t
+    lam_cm = grid_lambda_nm(grid.lam0_nm, grid.R, js) * 1e-7
+    nu = C / lam_cm
+    nu_lo, nu_hi = float(nu.min()), float(nu.max())
+    kap = np.zeros(len(js))
+    sl = np.zeros(len(js))
+    for i in range(0, L, chunk):
+        sub = lines.subset(slice(i, min(i + chunk, L)))
+        tt = physics.line_terms(sub, species_el, species_stage, el, pop, vturb)
+        # smallest |nu - nu0| over the sampled points is at least the distance to [nu_lo, nu_hi]
+        dmin = np.maximum(np.maximum(nu_lo - tt.nu0, tt.nu0 - nu_hi), 0.0)
+        keep = np.nonzero(tt.S * h_upper_bound(dmin / tt.dnuD, tt.a) >= thr)[0]
+        for n, j in enumerate(js):
+            v = (nu[n] - tt.nu0[keep]) / tt.dnuD[keep]
+            e = tt.S[keep] * H(v, tt.a[keep])
+            kap[n] += float(np.sum(e[e >= t]))
+            sl[n] += float(np.sum(e[np.abs(e / t - 1.0) <= slack_band]))
+    return kap, sl, kc

@@ -1637,13 +1637,14 @@ int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int au
                 cums.push_back(cum);
             }
             std::vector<RowDesc> rows = row_descs(b, tile, cums);
-            // sample: the tiles holding 16 fixed fractions of every row's grid
-            std::vector<int2> units;
+            // sample: up to 512 (row, tile) units spread evenly over all units of the batch, so
+            // that rows weigh by their tile counts as in the real launch
+            std::vector<int2> all;
             for (int i = 0; i < (int)rows.size(); ++i)
-                for (int q = 0; q < 16; ++q) {
-                    const int j = (int)((q + 0.5) / 16.0 * rows[i].N);
-                    units.push_back(make_int2(i, j / tile));
-                }
+                for (int t = 0; t < rows[i].nT; ++t) all.push_back(make_int2(i, t));
+            std::vector<int2> units;
+            const size_t step = std::max<size_t>(1, all.size() / 512);
+            for (size_t u = step / 2; u < all.size(); u += step) units.push_back(all[u]);
             int2* du;
             if ((r = balloc(b, &du, units.size()))) return r;
             MPSA_CUDA_TRY(cudaMemcpy(b->d_rows, rows.data(), rows.size() * sizeof(RowDesc), cudaMemcpyHostToDevice));

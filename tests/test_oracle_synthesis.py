@@ -88,3 +88,28 @@ def test_window_edges_and_sampling():
     ka, sa = sy.kappa_at(pl, js)
     assert np.allclose(ka, k[js], rtol=1e-13, atol=0)
     assert np.allclose(sa, slack[js], rtol=1e-13, atol=0)
+
+
+def test_chunked_sampled_opacity_equals_kappa_at():
+    # kappa_at_chunked (for lists too large to prepare at once) takes the same steps: on small
+    # lists, in several chunks, it reproduces kappa_at and the continuum of prepare
+    import workloads as wl
+    from oracle import synthesis as sy
+    for n_lines, lam, T, P in [(3000, (300.0, 303.0), 5000.0, 1e4), (800, (9.0, 10000.0), 12000.0, 1e8)]:
+        R = 2e6 if lam[1] < 1000 else 4000.0
+        w = wl.config_tiny(n_lines=n_lines, lam=lam, R=R, seed=17)
+        L = w.lines(); el = wl.elements(w.n_metals); se, ss = wl.species_table(w.n_metals)
+        pl = sy.prepare(L, se, ss, el, T, P, w.grid)
+        js = np.unique(np.random.default_rng(1).integers(0, pl.N, 25))
+        k1, s1 = sy.kappa_at(pl, js)
+        k2, s2, kc = sy.kappa_at_chunked(L, se, ss, el, T, P, w.grid, js, chunk=n_lines // 3 + 1)
+        assert abs(kc / pl.kappa_c - 1) < 1e-14
+        assert np.allclose(k2, k1, rtol=1e-12, atol=0) and np.allclose(s2, s1, rtol=1e-12, atol=0)
+
+
+def test_h_upper_bound():
+    from oracle import synthesis as sy
+    from oracle.voigt import H
+    v = np.r_[0.0, np.logspace(-3, 6, 200)]
+    for a in (1e-6, 1e-3, 0.1, 1.0, 30.0):
+        assert np.all(sy.h_upper_bound(v, a) >= H(v, a))
