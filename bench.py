@@ -64,7 +64,7 @@ def parse():
                    help="step: the throughput benchmark; serve: Poisson request stream through the server; "
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
-    p.add_argument("--batch-windows", type=int, default=24, help="spectrum windows in the batch sample")
+    p.add_argument("--batch-windows", type=int, default=200, help="spectrum windows in the batch sample")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the latency stream")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sub-measurement of the step mode")
     p.add_argument("--no-batch-leg", action="store_true", help="skip the batch sub-measurement of the step mode")
@@ -418,7 +418,7 @@ def native_arm(args):
     # and continuous batching against one request at a time (throughput, p50 / p99 latency)
     batch = serving = None
     if world == 1 and args.workload == "table" and not args.no_batch_leg:
-        batch = batch_measure(w, lines, el, se, ss, n_rows=2, n_windows=24, steps=2)
+        batch = batch_measure(w, lines, el, se, ss, n_rows=2, n_windows=200, steps=2)
     if world == 1 and args.workload == "table" and not args.no_serve:
         serving = serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=args.serve_seconds)
     cpu = None
@@ -473,14 +473,15 @@ def make_request_stream(rate, seconds, seed, spectrum_fraction=0.9, n_max=None):
     return out
 
 
-def serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=20.0, load=0.7, seed=2024, limit=120.0):
+def serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=20.0, load=0.7, seed=2024, drain_s=120.0):
     """Continuous batching against one request at a time, on the serving workload's request mix
     (90 % spectra of 40-120 depths over 1-500 nm windows at R = 5e5, 10 % ODFs of one composition
     over the 57 x 25 grid on 1-10 intervals).
       saturation: the same n_burst requests (the mix's proportions: 10 % ODFs) submitted at once;
         completed requests per second with 8 stream slots and with 1;
       latency: a Poisson stream offered at `load` times the one-slot saturation rate for
-        stream_s seconds, served with 8 slots and with 1; p50 / p99 of completion - arrival."""
+        stream_s seconds, served with 8 slots and with 1; p50 / p99 of completion - arrival.  Each
+        run ends when every request has completed or drain_s seconds after the last arrival."""
     from paper_2105_13611_gb300 import binding
     N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
     bounds_full = wl.equal_intervals(N, w.n_intervals)
@@ -502,6 +503,7 @@ def serve_measure(w, lines, el, se, ss, n_burst=20, stream_s=20.0, load=0.7, see
 
     def run(stream, max_inflight):
         srv = binding.Server(ctx, hbm_budget_bytes=int(120e9), max_inflight=max_inflight, rows_per_chunk=8)
+        limit = (stream[-1][0] if stream else 0.0) + drain_s
         t0 = time.perf_counter()
         pending, lat, i = [], {"spectrum": [], "odf": []}, 0
         while time.perf_counter() - t0 < limit:
@@ -567,7 +569,7 @@ def serve_arm(args):
     print(json.dumps(out), flush=True)
 
 
-def batch_measure(w, lines, el, se, ss, n_rows, n_windows, steps, seed=99):
+def batch_measure(w, lines, el, se, ss, n_rows, n_windows, steps, seed=99, autotune=True):
     """64 compositions x 1425 (T, P) rows plus spectrum windows (1-500 nm at R = 5e5): a seeded
     sample of n_rows ODF rows and n_windows windows runs (a) point by point through
     synth_opacity / build_odf and (b) as one persistent graph-captured batch; same results,
@@ -618,7 +620,7 @@ def batch_measure(w, lines, el, se, ss, n_rows, n_windows, steps, seed=99):
     torch.cuda.synchronize()
     t_plain = (time.perf_counter() - t0) / steps
     t0 = time.perf_counter()
-    batch = binding.Batch(ctx, groups, autotune=True)
+    batch = binding.Batch(ctx, groups, autotune=autotune)
     t_create = time.perf_counter() - t0
     batch.run()
     torch.cuda.synchronize()
@@ -853,6 +855,69 @@ def precision_arm(args):
             v.update({"opacity_vs_fp64_gpu_max_rel": float(rel.max()), "opacity_vs_fp64_gpu_p99_rel": float(np.quantile(rel, 0.99)),
                       "odf_vs_fp64_gpu_max_rel": float(ro.max()), "odf_vs_fp64_gpu_p99_rel": float(np.quantile(ro, 0.99))})
         out["variants"][names[prec]] = v
+    print(json.dumps(out), flush=True)
+
+
+def table_arm(args):
+    """The whole ODF table once: every (T, P) row of the 57 x 25 grid through synth_opacity and
+    build_odf, in chunks of 16 rows, timed with CUDA events per chunk (inputs resident: the
+    line list and the population table).  Prints the wall time, the line-evaluation rate and
+    the ODF (T, P) points per second of the whole table, and the slowest chunks."""
+    import torch
+
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    lines = w.lines()
+    el = wl.elements(w.n_metals)
+    se, ss = wl.species_table(w.n_metals)
+    ctx = binding.Context(0)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(el, w.T, w.P)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    K = w.n_intervals
+    bounds = wl.equal_intervals(N, K)
+    chunk = 16
+    rows = np.arange(len(w.T), dtype=np.int32)
+    kap = torch.empty((chunk, N), dtype=torch.float32, device="cuda")
+    kc = torch.empty(chunk, dtype=torch.float32, device="cuda")
+    ev = torch.empty(chunk, dtype=torch.int64, device="cuda")
+    odf = torch.empty((len(rows), K, len(w.widths)), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    opts = binding.make_opts(w.cut, w.kc_factor)
+    # warm-up on the first chunk
+    ctx.synth_opacity(w.grid, rows[:chunk], kap, kc, ev, opts=opts, stream=st)
+    ctx.build_odf(kap, bounds, w.widths, odf[:chunk], stream=st)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ctx.profile_enable(True)
+    ctx.profile_read(binding.KERNEL_PROFILE)
+    ctx.profile_read(binding.KERNEL_ODF)
+    evs, per_chunk = 0, []
+    t0 = time.perf_counter()
+    for i in range(0, len(rows), chunk):
+        sel = rows[i:i + chunk]
+        n = len(sel)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctx.synth_opacity(w.grid, sel, kap[:n], kc[:n], ev[:n], opts=opts, stream=st)
+        ctx.build_odf(kap[:n], bounds, w.widths, odf[i:i + n], stream=st)
+        e1.record(st)
+        e1.synchronize()
+        per_chunk.append((int(sel[0]), int(sel[-1]), e0.elapsed_time(e1) / 1e3, int(ev[:n].sum())))
+        evs += per_chunk[-1][3]
+    wall = time.perf_counter() - t0
+    tiles_ms, _ = ctx.profile_read(binding.KERNEL_PROFILE)
+    odf_ms, _ = ctx.profile_read(binding.KERNEL_ODF)
+    clk = clocks.stop()
+    gpu_s = sum(c[2] for c in per_chunk)
+    slow = sorted(per_chunk, key=lambda c: -c[2])[:5]
+    out = {"mode": "table", "metric": "whole 57 x 25 ODF table: wall time, line-evals/s, ODF (T,P) points/s",
+           "rows": len(rows), "grid_points": N, "intervals": K, "lines": len(lines), "chunk_rows": chunk,
+           "wall_s": wall, "gpu_s": gpu_s, "evals": evs, "evals_per_s": evs / gpu_s,
+           "odf_points_per_s": len(rows) / gpu_s, "k_tiles_s": tiles_ms / 1e3, "k_odf_s": odf_ms / 1e3,
+           "slowest_chunks": [{"rows": [a, b], "s": t, "evals": e} for a, b, t, e in slow],
+           "clocks": clk, "data": "synthetic"}
     print(json.dumps(out), flush=True)
 
 

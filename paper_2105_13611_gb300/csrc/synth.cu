@@ -1637,13 +1637,15 @@ int batch_build(mpsa_batch* b, const mpsa_batch_group* gin, int n_groups, int au
                 cums.push_back(cum);
             }
             std::vector<RowDesc> rows = row_descs(b, tile, cums);
-            // sample: up to 512 (row, tile) units spread evenly over all units of the batch, so
-            // that rows weigh by their tile counts as in the real launch
+            // sample: at least 2048 (row, tile) units (all of them if there are fewer) spread
+            // evenly over all units of the batch, so that rows weigh by their tile counts as in
+            // the real launch and every CTA of the persistent launch runs several units (the
+            // time then measures throughput, not the slowest unit)
             std::vector<int2> all;
             for (int i = 0; i < (int)rows.size(); ++i)
                 for (int t = 0; t < rows[i].nT; ++t) all.push_back(make_int2(i, t));
             std::vector<int2> units;
-            const size_t step = std::max<size_t>(1, all.size() / 512);
+            const size_t step = std::max<size_t>(1, all.size() / 2048);
             for (size_t u = step / 2; u < all.size(); u += step) units.push_back(all[u]);
             int2* du;
             if ((r = balloc(b, &du, units.size()))) return r;

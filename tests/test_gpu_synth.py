@@ -213,3 +213,46 @@ def test_table_workload_sampled():
             x = kap[i, int(b[k]):int(b[k + 1])].cpu().numpy().astype(np.float64)
             o = od.odf(x, [0, len(x)], w.widths)[0]
             assert np.all(np.abs(og[k] - o) <= 1e-5 * np.abs(o) + 1e-300), (r, k)
+
+
+def test_no_line_passes_the_cut():
+    # a cut far above every line's centre opacity: no window, zero opacity and zero evaluations
+    # on every row (the degenerate case of the cut rule); the continuum stays defined
+    import torch
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_tiny(n_lines=50, lam=(300.0, 300.3), seed=71)
+    ctx, L = gpu_context(w)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    kap = torch.full((4, N), -1.0, dtype=torch.float32, device="cuda")
+    kc = torch.empty(4, dtype=torch.float32, device="cuda")
+    ev = torch.empty(4, dtype=torch.int64, device="cuda")
+    ctx.synth_opacity(w.grid, np.arange(4), kap, kc, ev, opts=binding.make_opts(cut=1e12))
+    torch.cuda.synchronize()
+    assert float(kap.abs().max()) == 0.0 and int(ev.sum()) == 0
+    for s in range(4):
+        pl = sy.prepare(L, *wl.species_table(w.n_metals), wl.elements(w.n_metals), w.T[s], w.P[s], w.grid,
+                        1e12, w.kc_factor)
+        assert abs(float(kc[s]) / pl.kappa_c - 1) < 1e-5
+        lo, hi = sy.windows(pl)
+        assert np.all(hi < lo)
+
+
+def test_single_point_and_single_line():
+    # a one-point grid and a one-line list
+    import torch
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_tiny(n_lines=1, lam=(400.0, 400.0001), seed=72)
+    ctx, L = gpu_context(w)
+    N = binding.grid_size(w.grid.lam0_nm, w.grid.lam1_nm, w.grid.R)
+    kap = torch.empty((4, N), dtype=torch.float32, device="cuda")
+    kc = torch.empty(4, dtype=torch.float32, device="cuda")
+    ctx.synth_opacity(w.grid, np.arange(4), kap, kc)
+    cont = torch.empty((4, N), dtype=torch.float32, device="cuda")
+    ctx.synth_continuum(w.grid, np.arange(4), cont)
+    torch.cuda.synchronize()
+    kg = kap.cpu().numpy()
+    for s in range(4):
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        bad, _, _ = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0
+    assert np.all(np.isfinite(cont.cpu().numpy())) and float(cont.min()) > 0
