@@ -45,8 +45,8 @@ FLOP_PER_EVAL = 6.5
 FP32_LANES_PER_SM = 128
 # kernels of the library per timed step: synth_opacity (k_place, k_consts, k_kappa0, k_med_init,
 # three k_med_hist + k_med_pick levels, k_prep, k_scan_class, k_scan_fin, k_scatter, k_ranges,
-# k_tiles) and build_odf (k_odf)
-LAUNCHES_PER_STEP = 17
+# k_tiles) and build_odf (k_odf_gather, then k_odf for the intervals it leaves)
+LAUNCHES_PER_STEP = 18
 
 
 def parse():
@@ -65,7 +65,7 @@ def parse():
                         "batch: persistent graph-captured batch against the plain per-point path")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
     p.add_argument("--batch-windows", type=int, default=200, help="spectrum windows in the batch sample")
-    p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the latency stream")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the latency stream")
     p.add_argument("--no-serve", action="store_true", help="skip the serving sub-measurement of the step mode")
     p.add_argument("--no-batch-leg", action="store_true", help="skip the batch sub-measurement of the step mode")
     p.add_argument("--bin-rays", type=int, default=8192, help="rays per step of the bin-intensity form")
@@ -411,7 +411,8 @@ def native_arm(args):
     odf_bytes = B * N * 4 + B * K * 12 * 8
     roofline_odf = {"bound": "hbm", "achieved": odf_bytes / (odf_avg / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": odf_bytes / (odf_avg / 1e3) / 1e9 / hbm,
-                    "traffic": measured_traffic("k_odf", ["odf.cu", "common.cuh"], sel), "kernel": "k_odf (build_odf)",
+                    "traffic": measured_traffic("build_odf", ["odf.cu", "common.cuh"], sel),
+                    "kernel": "build_odf: k_odf_gather, then k_odf on the intervals it leaves",
                     "peak_kind": f"{peak_kind} HBM copy bandwidth", "avg_launch_ms": odf_avg, "launches": odf_n}
     ctx.close()
     # the other parts of the headline metric: the batched form against the plain per-point path,

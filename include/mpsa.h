@@ -255,9 +255,16 @@ int synth_continuum(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const 
  *     reaches into zero values has geometric mean 0).
  *   odf_out (device, double[n_rows][K][n_steps]).
  *   n_rows: 1..65535 rows per call (one launch; split larger tables).
- * Order statistics are found by a 4-level radix multi-select (12, 7, 6 and 6
- * bits) on the FP32 bit patterns with exact integer partial sums; only the final
- * cross-exponent reduction is FP64.  Geometric means take one more pass that sums ln kappa
+ * The order statistics at the boundaries are exact.  Arithmetic means with
+ * n_steps <= 12 on intervals of at most 65,536 points are computed by a count
+ * pass over 14-bit prefixes of the FP32 patterns and a gather pass.  The gather
+ * sums the values between the boundaries' bins in FP32 per lane: relative error
+ * at most 3.8e-6, about 1e-7 in practice.  It sums the boundaries' own bins
+ * exactly as integers.  A second kernel recomputes, by the multi-select below,
+ * any interval whose boundary bins hold more than 8,192 values.  Every other
+ * case uses a 4-level radix multi-select (12, 7, 6 and 6 bits) on the FP32 bit
+ * patterns with exact integer partial sums; only the final cross-exponent
+ * reduction is FP64.  Geometric means take one more pass that sums ln kappa
  * (exponent in FP64, mantissa by FP32 logf) between consecutive order
  * statistics in FP64.  Stream-ordered, no host synchronisation.
  * Errors: MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.

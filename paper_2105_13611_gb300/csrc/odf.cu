@@ -1,5 +1,9 @@
 // build_odf: opacity distribution functions (paper Sect. 2.3 and App. E).
 //
+// Two kernels.  k_odf_gather (further below) serves arithmetic means with at most 12 steps on
+// intervals of at most 65,536 points by a count pass and a gather pass; k_odf, the exact
+// multi-select described here, serves every other case and the intervals the gather leaves.
+//
 // For each (row, interval) one CTA finds the order statistics at the sub-bin
 // boundaries and the sums of all values below them, then forms the step means
 //   m_s = (S(c_s n) - S(c_{s-1} n)) / (w_s n),
@@ -58,6 +62,9 @@ constexpr int kCand = ODF_KCAND;                   // candidate buffer (32-bit p
 constexpr long long kMaxInterval = 1ll << 21;      // count < 2^24 and low-bit sums < 2^40 per bin
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxOdfRows = 65535;                // gridDim.y of the ODF launch
+// The first output word of an interval that k_odf_gather leaves to k_odf: a NaN pattern that
+// arithmetic never produces (its payload is not the canonical one).
+constexpr unsigned long long kOdfRedo = 0x7ff40d0f0d0f0d0full;
 constexpr int kMaxDevices = 64;
 
 struct Target {
@@ -333,7 +340,7 @@ __device__ __forceinline__ void resolve_warp(Target& t, const Hist& h, int wb, i
 __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __restrict__ kappa, int64_t N, int K,
                                                      const int64_t* __restrict__ bounds, int n_steps,
                                                      const double* __restrict__ cw, const double* __restrict__ w,
-                                                     double* __restrict__ out, int geom) {
+                                                     double* __restrict__ out, int geom, int redo_only) {
     extern __shared__ __align__(16) unsigned sm[];
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
@@ -362,6 +369,9 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
     __shared__ int n_thr;
 
     const int k = blockIdx.x, row = blockIdx.y;
+    // after k_odf_gather: only the intervals it marked for this kernel (a uniform early exit)
+    if (redo_only && *reinterpret_cast<const unsigned long long*>(out + ((size_t)row * K + k) * n_steps) != kOdfRedo)
+        return;
     const int64_t b0 = bounds[k], b1 = bounds[k + 1];
     const long long n = b1 - b0;
     const float* x = kappa + (size_t)row * N + b0;
@@ -691,6 +701,450 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_odf_gather: arithmetic means for intervals of at most 65,536 points and at most 12 steps
+// (the ODFs of the paper: 328 intervals x 12 steps), count then gather.
+//
+// Pass 1 (HBM) counts the values of each 14-bit prefix of the FP32 pattern (bits 30..17: the
+// exponent and six mantissa bits, 64 bins per octave) with one shared-memory add per value and
+// no other work, so it runs at the rate of the loads.  A scan of the counts gives the bin of
+// every boundary rank (a target bin) and the number of values below that bin.  A byte table
+// then maps each bin to its gap (the bins between two consecutive target bins, numbered from
+// 0) or marks it as a target bin.  Pass 2 (from L2) adds each value of a gap to a lane-private
+// FP32 column of that gap in shared memory (columns [bank][warp][gap][lane]: no two lanes share
+// an address, so no atomics; two banks give every lane two independent read-add-write chains)
+// and sets a bit for each value in a target bin; those few (1-3 % of the values on the table
+// workload) go to their target bin's region of a candidate list.  All values of a target bin
+// share the exponent, so one warp per target bin finds each order statistic by two radix
+// levels over its candidates (bits 16..8, then 7..0) and sums the candidates below it exactly,
+// as integers in units of the exponent's ulp.
+//
+// Sums: a column holds at most 64 values (65,536 points over 512 threads and two banks), a
+// relative error below 63 * 2^-24 = 3.8e-6 even if every rounding errs the same way, about
+// 1e-7 in practice.  The columns of a gap are added as FP32 pairs (hi, lo) with error-free
+// two-sums (FP64 adds run at 1/64 of the FP32 rate on this part), then converted to FP64.  An
+// interval whose target bins hold more values than the candidate list, or that is longer than
+// 65,536 points, gets kOdfRedo in its first output word and is recomputed by k_odf, which also
+// serves more steps and the geometric means.
+constexpr int kGThreads = 512;
+constexpr int kGWarps = kGThreads / 32;
+constexpr int kGShift = 17;                              // bin = bits 30..17
+constexpr int kGBins = 1 << (31 - kGShift);              // 16384
+constexpr int kGMaxN = 1 << 16;
+constexpr int kGMaxSteps = 12;
+constexpr int kGGaps = kGMaxSteps;                       // gaps 0..n_slots, n_slots <= 11
+constexpr int kGBanks = 2;
+constexpr int kGCand = 8192;                             // candidate list (32-bit patterns)
+constexpr int kGColWords = kGWarps * kGGaps * 32;        // one bank of columns [warp][gap][lane]
+constexpr int kGTableWords = kGBins / 4;                 // one byte per bin
+constexpr size_t kGSmem = ((size_t)kGTableWords + kGCand + (size_t)kGBanks * kGColWords) * sizeof(unsigned);  // 96 KB
+constexpr int kGU = 4;                                   // float4 loads in flight per thread
+static_assert(kGSmem >= (size_t)kGBins * sizeof(unsigned), "the counts must fit the dynamic shared memory");
+static_assert((kGMaxSteps - 1) * 512 <= kGBanks * kGColWords, "selection histograms reuse the columns");
+
+__device__ __forceinline__ unsigned gbin(unsigned bits) { return (bits >> kGShift) & (kGBins - 1); }
+
+// (hi, lo) += a, with the rounding error of hi + a kept exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float a) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (a - bp);
+    hi = s;
+}
+
+__global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __restrict__ kappa, int64_t N, int K,
+                                                             const int64_t* __restrict__ bounds, int n_steps,
+                                                             const double* __restrict__ cw,
+                                                             const double* __restrict__ w, double* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned sm[];
+    __shared__ int s_tbase[kGThreads];    // values below each thread's 32 bins
+    __shared__ int s_kt[kGMaxSteps];      // rank of each boundary (>= n: the total)
+    __shared__ int s_tbin[kGMaxSteps];    // its bin
+    __shared__ int s_blt[kGMaxSteps];     // values below its bin
+    __shared__ int s_bcnt[kGMaxSteps];    // values in its bin
+    __shared__ int s_tslot[kGMaxSteps];   // its slot (distinct target bin), -1 for the total
+    __shared__ int s_sbin[kGMaxSteps], s_slt[kGMaxSteps];   // per slot: bin, values below it
+    __shared__ int s_coff[kGMaxSteps + 1], s_ccur[kGMaxSteps];   // per slot: candidate region, cursor
+    __shared__ unsigned s_theta[kGMaxSteps];
+    __shared__ int s_cb[kGMaxSteps];      // values below the order statistic
+    __shared__ double s_sb[kGMaxSteps];   // sum of its slot's values below it
+    __shared__ double s_G[kGGaps], s_T[kGMaxSteps], s_P[kGMaxSteps + 1];
+    __shared__ int s_wsum[kGWarps];
+    __shared__ int s_nslots;
+
+    const int k = blockIdx.x, row = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t b0 = bounds[k];
+    const int64_t len = bounds[k + 1] - b0;
+    double* o = out + ((size_t)row * K + k) * n_steps;
+    if (len > kGMaxN) {   // uniform: left to k_odf
+        if (tid == 0) *reinterpret_cast<unsigned long long*>(o) = kOdfRedo;
+        return;
+    }
+    const int n = (int)len, nt = n_steps - 1;
+    const float* x = kappa + (size_t)row * N + b0;
+    unsigned* cnt = sm;                                                          // pass 1: [kGBins]
+    unsigned char* tbl = reinterpret_cast<unsigned char*>(sm);                   // pass 2: [kGBins]
+    unsigned* cand = sm + kGTableWords;                                          // [kGCand]
+    float* col = reinterpret_cast<float*>(sm + kGTableWords + kGCand);           // [kGBanks][kGColWords]
+
+    // u = c_s n as one rounded FP64 product, as in k_odf and the oracle
+    if (tid < nt) s_kt[tid] = (int)floor(__dmul_rn(cw[tid + 1], (double)n));
+    for (int i = tid; i < kGBins / 4; i += kGThreads) reinterpret_cast<uint4*>(cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+
+    // the 16-byte-aligned body as float4, strided over the CTA (512 contiguous bytes per warp
+    // and load); the unaligned head and tail (< 4 values each) go to threads 0..3
+    const int mis = (int)(((uintptr_t)x >> 2) & 3u);
+    const int head = min(mis ? 4 - mis : 0, n);
+    const float4* body = reinterpret_cast<const float4*>(x + head);
+    const int nv = (n - head) >> 2;
+    const int tail0 = head + 4 * nv;
+
+    // ---- pass 1 (HBM): counts
+    for (int i0 = 0; i0 < nv; i0 += kGU * kGThreads) {
+        float4 q[kGU];
+#pragma unroll
+        for (int u = 0; u < kGU; ++u) {
+            const int i = i0 + u * kGThreads + tid;
+            q[u] = i < nv ? __ldg(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kGU; ++u)
+            if (i0 + u * kGThreads + tid < nv) {
+                atomicAdd(cnt + gbin(__float_as_uint(q[u].x)), 1u);
+                atomicAdd(cnt + gbin(__float_as_uint(q[u].y)), 1u);
+                atomicAdd(cnt + gbin(__float_as_uint(q[u].z)), 1u);
+                atomicAdd(cnt + gbin(__float_as_uint(q[u].w)), 1u);
+            }
+    }
+    if (tid < head) atomicAdd(cnt + gbin(__float_as_uint(__ldg(x + tid))), 1u);
+    if (tid < n - tail0) atomicAdd(cnt + gbin(__float_as_uint(__ldg(x + tail0 + tid))), 1u);
+    __syncthreads();
+
+    // ---- scan: thread tid owns bins [32 tid, 32 tid + 32) (rotated reads: no bank conflicts)
+    {
+        int tot = 0;
+        const uint4* c4 = reinterpret_cast<const uint4*>(cnt) + tid * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint4 q = c4[(j + lane) & 7];
+            tot += (int)(q.x + q.y + q.z + q.w);
+        }
+        int incl = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int below = incl - tot;
+        for (int v = 0; v < warp; ++v) below += s_wsum[v];
+        s_tbase[tid] = below;
+    }
+    __syncthreads();
+    // one warp per boundary rank: the thread range holding it (the last base <= rank), then its
+    // bin among that thread's 32 (a warp scan) and the values below the bin
+    if (warp < nt) {
+        const int t = warp, kt = s_kt[t];
+        if (kt < n) {
+            int lo = 0, hi = kGThreads - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_tbase[mid] <= kt) lo = mid;
+                else hi = mid - 1;
+            }
+            const int c = (int)cnt[lo * 32 + lane];
+            int ci = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(kFull, ci, d);
+                if (lane >= d) ci += y;
+            }
+            const int rel = kt - s_tbase[lo];
+            const unsigned m = __ballot_sync(kFull, rel < ci);
+            if (lane == (m ? __ffs(m) - 1 : 31)) {
+                s_tbin[t] = lo * 32 + lane;
+                s_blt[t] = s_tbase[lo] + ci - c;
+                s_bcnt[t] = c;
+            }
+        }
+    }
+    __syncthreads();
+    // distinct target bins -> slots and candidate regions (warp 0, lane t = target t; the bins
+    // are non-decreasing in t, so a slot starts where a target's bin differs from the previous one)
+    if (warp == 0) {
+        const bool act = lane < nt && s_kt[lane] < n;
+        const int bin = act ? s_tbin[lane] : -1;
+        const int prev = __shfl_up_sync(kFull, bin, 1);
+        const bool start = act && (lane == 0 || prev != bin);
+        const unsigned starts = __ballot_sync(kFull, start);
+        const int slot = act ? __popc(starts & ((2u << lane) - 1u)) - 1 : -1;
+        if (lane < nt) s_tslot[lane] = slot;
+        const int c = start ? s_bcnt[lane] : 0;
+        int ci = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, ci, d);
+            if (lane >= d) ci += y;
+        }
+        if (start) {
+            s_sbin[slot] = bin;
+            s_slt[slot] = s_blt[lane];
+            s_coff[slot] = ci - c;
+            s_ccur[slot] = ci - c;
+        }
+        if (lane == 31) {
+            s_coff[__popc(starts)] = ci;
+            s_nslots = __popc(starts);
+        }
+    }
+    __syncthreads();
+    const int ns = s_nslots;
+    if (s_coff[ns] > kGCand) {   // uniform: left to k_odf
+        if (tid == 0) *reinterpret_cast<unsigned long long*>(o) = kOdfRedo;
+        return;
+    }
+    // ---- code table over the dead counts: gap index, or 0x80 | slot for a target bin
+    {
+        const int bA = tid * 32;
+        int g = 0;
+        for (int j = 0; j < ns; ++j) g += s_sbin[j] < bA;
+        uint4 v0, v1;
+        if (g < ns && s_sbin[g] < bA + 32) {
+            unsigned wd[8];
+            int nx = s_sbin[g];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                unsigned code;
+                if (bA + j == nx) {
+                    code = 0x80u | (unsigned)g;
+                    ++g;
+                    nx = g < ns ? s_sbin[g] : 0x7fffffff;
+                } else {
+                    code = (unsigned)g;
+                }
+                if ((j & 3) == 0) wd[j >> 2] = 0u;
+                wd[j >> 2] |= code << (8 * (j & 3));
+            }
+            v0 = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            v1 = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        } else {
+            const unsigned wv = (unsigned)g * 0x01010101u;
+            v0 = v1 = make_uint4(wv, wv, wv, wv);
+        }
+        uint4* t4 = reinterpret_cast<uint4*>(tbl) + tid * 2;
+        t4[0] = v0;
+        t4[1] = v1;
+    }
+    for (int i = tid; i < kGBanks * kGColWords / 4; i += kGThreads)
+        reinterpret_cast<uint4*>(col)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+
+    // ---- pass 2 (L2): gap columns and candidates.  All 16 codes of an iteration are read
+    // before any column is written, and the two banks take alternate values, so each lane's
+    // read-add-write steps form two independent chains.
+    {
+        float* colA = col + warp * (kGGaps * 32) + lane;
+        float* colB = colA + kGColWords;
+        auto to_cand = [&](unsigned bits) {
+            const int pos = atomicAdd(&s_ccur[tbl[bits >> kGShift] & 0x7fu], 1);
+            cand[pos] = bits;   // inside the slot's region: its size is the bin's count
+        };
+        for (int i0 = 0; i0 < nv; i0 += kGU * kGThreads) {
+            float4 q[kGU];
+#pragma unroll
+            for (int u = 0; u < kGU; ++u) {
+                const int i = i0 + u * kGThreads + tid;
+                q[u] = i < nv ? __ldcs(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float v[4 * kGU];
+            unsigned cd[4 * kGU];
+#pragma unroll
+            for (int u = 0; u < kGU; ++u) {
+                const bool ok = i0 + u * kGThreads + tid < nv;
+                const float qq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const unsigned bits = __float_as_uint(qq[c]) & 0x7fffffffu;
+                    v[4 * u + c] = __uint_as_float(bits);
+                    cd[4 * u + c] = ok ? tbl[bits >> kGShift] : 0xffu;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4 * kGU; e += 2) {
+                const unsigned ca = cd[e], cb = cd[e + 1];
+                float a = 0.f, b = 0.f;
+                if (ca < (unsigned)kGGaps) a = colA[ca * 32];
+                if (cb < (unsigned)kGGaps) b = colB[cb * 32];
+                if (ca < (unsigned)kGGaps) colA[ca * 32] = a + v[e];
+                if (cb < (unsigned)kGGaps) colB[cb * 32] = b + v[e + 1];
+            }
+            unsigned cm = 0u;
+#pragma unroll
+            for (int e = 0; e < 4 * kGU; ++e)
+                if (cd[e] >= 0x80u && cd[e] != 0xffu) cm |= 1u << e;
+            while (cm) {   // rare: reload the value (an L1/L2 hit) rather than keep it
+                const int e = __ffs(cm) - 1;
+                cm &= cm - 1u;
+                const int i = i0 + (e >> 2) * kGThreads + tid;
+                to_cand(__float_as_uint(__ldg(x + head + 4 * i + (e & 3))) & 0x7fffffffu);
+            }
+        }
+        auto one = [&](unsigned bits) {
+            bits &= 0x7fffffffu;
+            const unsigned code = tbl[bits >> kGShift];
+            if (code < (unsigned)kGGaps) colA[code * 32] += __uint_as_float(bits);
+            else to_cand(bits);
+        };
+        if (tid < head) one(__float_as_uint(__ldg(x + tid)));
+        if (tid < n - tail0) one(__float_as_uint(__ldg(x + tail0 + tid)));
+    }
+    __syncthreads();
+
+    // ---- gap sums (one warp per gap): FP32 two-sums over the 32 columns of a lane, then over
+    // the lanes, then FP64
+    if (warp <= ns) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+        for (int v = 0; v < kGBanks * kGWarps; ++v) two_sum_add(hi, lo, col[v * (kGGaps * 32) + warp * 32 + lane]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const float h2 = __shfl_down_sync(kFull, hi, d), l2 = __shfl_down_sync(kFull, lo, d);
+            two_sum_add(hi, lo, h2);
+            lo += l2;
+        }
+        if (lane == 0) s_G[warp] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+
+    // ---- one warp per slot: its total and the order statistics of its targets (the columns
+    // are dead: their memory holds one 512-bin histogram per slot)
+    if (warp < ns) {
+        const int j = warp;
+        const unsigned B = (unsigned)s_sbin[j];
+        const unsigned E = B >> (23 - kGShift);
+        const int eff = E >= 1 ? (int)E : 1;
+        const unsigned impl = E >= 1 ? 0x800000u : 0u;
+        const int c0 = s_coff[j], c1 = s_coff[j + 1];
+        unsigned* h = reinterpret_cast<unsigned*>(col) + j * 512;
+        unsigned long long ts = 0;   // mantissa integers: < 2^24 * 2^16
+        for (int i = c0 + lane; i < c1; i += 32) ts += (cand[i] & 0x7fffffu) | impl;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) ts += __shfl_down_sync(kFull, ts, d);
+        if (lane == 0) s_T[j] = ldexp((double)ts, eff - 150);
+        for (int t = 0; t < nt; ++t) {
+            if (s_tslot[t] != j) continue;   // uniform over the warp
+            const int r = s_kt[t] - s_slt[j];   // rank inside the bin (below its count)
+            // level A: bits 16..8
+            for (int i = lane; i < 512; i += 32) h[i] = 0u;
+            __syncwarp();
+            for (int i = c0 + lane; i < c1; i += 32) atomicAdd(h + ((cand[i] >> 8) & 511u), 1u);
+            __syncwarp();
+            int cl = 0;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) cl += (int)h[lane * 16 + m];
+            int ci = cl;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(kFull, ci, d);
+                if (lane >= d) ci += y;
+            }
+            unsigned ow = __ballot_sync(kFull, r >= ci - cl && r < ci);
+            int owner = ow ? __ffs(ow) - 1 : 0;
+            int a = 0, cA = 0;
+            if (lane == owner) {
+                int run = ci - cl, m = 0;
+                for (; m < 15; ++m) {
+                    const int c = (int)h[lane * 16 + m];
+                    if (r < run + c) break;
+                    run += c;
+                }
+                a = lane * 16 + m;
+                cA = run;
+            }
+            a = __shfl_sync(kFull, a, owner);
+            cA = __shfl_sync(kFull, cA, owner);
+            __syncwarp();
+            // level B: bits 7..0 of the values in level-A bin a
+            for (int i = lane; i < 256; i += 32) h[i] = 0u;
+            __syncwarp();
+            for (int i = c0 + lane; i < c1; i += 32) {
+                const unsigned c = cand[i];
+                if (((c >> 8) & 511u) == (unsigned)a) atomicAdd(h + (c & 255u), 1u);
+            }
+            __syncwarp();
+            const int r2 = r - cA;
+            cl = 0;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) cl += (int)h[lane * 8 + m];
+            ci = cl;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(kFull, ci, d);
+                if (lane >= d) ci += y;
+            }
+            ow = __ballot_sync(kFull, r2 >= ci - cl && r2 < ci);
+            owner = ow ? __ffs(ow) - 1 : 0;
+            int bb = 0, cB = 0;
+            if (lane == owner) {
+                int run = ci - cl, m = 0;
+                for (; m < 7; ++m) {
+                    const int c = (int)h[lane * 8 + m];
+                    if (r2 < run + c) break;
+                    run += c;
+                }
+                bb = lane * 8 + m;
+                cB = run;
+            }
+            bb = __shfl_sync(kFull, bb, owner);
+            cB = __shfl_sync(kFull, cB, owner);
+            const unsigned theta = (B << kGShift) | ((unsigned)a << 8) | (unsigned)bb;
+            unsigned long long sb = 0;
+            for (int i = c0 + lane; i < c1; i += 32) {
+                const unsigned c = cand[i];
+                if (c < theta) sb += (c & 0x7fffffu) | impl;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sb += __shfl_down_sync(kFull, sb, d);
+            if (lane == 0) {
+                s_theta[t] = theta;
+                s_cb[t] = s_slt[j] + cA + cB;
+                s_sb[t] = ldexp((double)sb, eff - 150);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+
+    // ---- step means: S(u) = (sum below theta) + (u - #below) theta at each boundary; s_P[j] is
+    // the sum of everything below slot j's bin (an FP64 scan over the slots in warp 0), s_P[ns]
+    // the total
+    if (warp == 0) {
+        const double gj = lane <= ns ? s_G[lane] : 0.0;
+        const double v = gj + (lane < ns ? s_T[lane] : 0.0);
+        double inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane < ns) s_P[lane] = inc - v + gj;
+        if (lane == ns) s_P[ns] = inc;
+    }
+    __syncthreads();
+    if (tid < n_steps) {
+        auto S = [&](int bidx) -> double {
+            if (bidx == 0) return 0.0;
+            if (bidx == n_steps || s_kt[bidx - 1] >= n) return s_P[ns];
+            const int t = bidx - 1;
+            const double u = __dmul_rn(cw[bidx], (double)n);
+            return s_P[s_tslot[t]] + s_sb[t] + (u - (double)s_cb[t]) * (double)__uint_as_float(s_theta[t]);
+        };
+        o[tid] = (S(tid + 1) - S(tid)) / (w[tid] * (double)n);
+    }
+}
+
 size_t odf_smem_bytes(int n_steps) {
     const int nt = n_steps - 1;
     const int nslots = nt > kMinSlots ? nt : kMinSlots;
@@ -746,6 +1200,8 @@ int odf_setup() {
     std::call_once(once[dev], [&] {
         err[dev] = cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)odf_smem_bytes(kMaxSteps));
+        if (err[dev] == cudaSuccess)
+            err[dev] = cudaFuncSetAttribute(k_odf_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
     });
     if (err[dev] != cudaSuccess)
         return fail(MPSA_ECUDA, "build_odf: cudaFuncSetAttribute: %s", cudaGetErrorString(err[dev]));
@@ -756,8 +1212,16 @@ int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* 
                const double* d_cw, const double* d_w, double* d_out, int mean_kind, cudaStream_t st) {
     int r;
     if ((r = odf_setup())) return r;
+    // arithmetic means with at most 12 steps: count then gather, and the exact multi-select
+    // only for the intervals the gather leaves (too long, or too many candidates); otherwise the
+    // multi-select for every interval
+    const bool gather = mean_kind == MPSA_MEAN_ARITH && n_steps <= kGMaxSteps;
+    if (gather) {
+        k_odf_gather<<<dim3(K, n_rows), kGThreads, kGSmem, st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w, d_out);
+        MPSA_CUDA_TRY(cudaGetLastError());
+    }
     k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w,
-                                                                         d_out, mean_kind == MPSA_MEAN_GEOM);
+                                                                         d_out, mean_kind == MPSA_MEAN_GEOM, gather);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }
