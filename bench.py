@@ -28,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving legs run 16 CUDA streams (8 slots, two priorities each); with the default of 8
+# hardware queues, streams share queues and a small request can wait behind another's kernels
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 

@@ -255,18 +255,19 @@ int synth_continuum(mpsa_ctx* ctx, const mpsa_lgrid* grid, int32_t n_sel, const 
  *     reaches into zero values has geometric mean 0).
  *   odf_out (device, double[n_rows][K][n_steps]).
  *   n_rows: 1..65535 rows per call (one launch; split larger tables).
- * The order statistics at the boundaries are exact.  Arithmetic means with
- * n_steps <= 12 on intervals of at most 65,536 points are computed by a count
- * pass over 14-bit prefixes of the FP32 patterns and a gather pass.  The gather
- * sums the values between the boundaries' bins in FP32 per lane: relative error
- * at most 3.8e-6, about 1e-7 in practice.  It sums the boundaries' own bins
- * exactly as integers.  A second kernel recomputes, by the multi-select below,
- * any interval whose boundary bins hold more than 8,192 values.  Every other
- * case uses a 4-level radix multi-select (12, 7, 6 and 6 bits) on the FP32 bit
- * patterns with exact integer partial sums; only the final cross-exponent
- * reduction is FP64.  Geometric means take one more pass that sums ln kappa
- * (exponent in FP64, mantissa by FP32 logf) between consecutive order
- * statistics in FP64.  Stream-ordered, no host synchronisation.
+ * The order statistics at the boundaries are exact.  With n_steps <= 12 on
+ * intervals of at most 65,536 points, a count pass over 14-bit prefixes of the
+ * FP32 patterns and a gather pass compute both kinds of mean.  Arithmetic sums
+ * of the values between the boundaries' bins are FP32 per lane: relative error
+ * at most 3.8e-6, about 1e-7 in practice.  The boundaries' own bins are summed
+ * exactly as integers, and so are all the geometric means' ln sums (units of
+ * 2^-30).  A second kernel recomputes, by the multi-select below, any interval
+ * whose boundary bins hold more than 8,192 values.  Every other case uses a
+ * 4-level radix multi-select (12, 7, 6 and 6 bits) on the FP32 bit patterns
+ * with exact integer partial sums; only the final cross-exponent reduction is
+ * FP64, and geometric means take one more pass that sums ln kappa between
+ * consecutive order statistics.  ln kappa is the exponent times ln 2 plus FP32
+ * logf of the mantissa.  Stream-ordered, no host synchronisation.
  * Errors: MPSA_EINVAL, MPSA_ENOMEM, MPSA_ECUDA.
  */
 int build_odf(mpsa_ctx* ctx, const float* kappa, int32_t n_rows, int64_t N,
@@ -421,7 +422,10 @@ void mpsa_batch_destroy(mpsa_batch* b);
  * Requests wait in FIFO order; the oldest is started as soon as one of
  * max_inflight stream slots is free and its estimated device memory fits the
  * budget, so requests arriving while others run are admitted without waiting
- * for them and their kernels overlap on the device.  Each request runs exactly
+ * for them and their kernels overlap on the device.  Spectrum requests run on
+ * streams of the device's highest priority and ODF requests on its lowest, so
+ * the block scheduler starts a spectrum's CTAs ahead of an ODF request's
+ * queued ones (running CTAs are not preempted).  Each request runs exactly
  * the kernels of the direct entry points (synthesis in chunks of
  * rows_per_chunk rows to bound scratch), so its result does not depend on what
  * else is in flight.

@@ -1,7 +1,7 @@
 // build_odf: opacity distribution functions (paper Sect. 2.3 and App. E).
 //
-// Two kernels.  k_odf_gather (further below) serves arithmetic means with at most 12 steps on
-// intervals of at most 65,536 points by a count pass and a gather pass; k_odf, the exact
+// Two kernels.  k_odf_gather (further below) serves both kinds of mean with at most 12 steps
+// on intervals of at most 65,536 points by a count pass and a gather pass; k_odf, the exact
 // multi-select described here, serves every other case and the intervals the gather leaves.
 //
 // For each (row, interval) one CTA finds the order statistics at the sub-bin
@@ -702,8 +702,8 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
 }
 
 // ---------------------------------------------------------------------------
-// k_odf_gather: arithmetic means for intervals of at most 65,536 points and at most 12 steps
-// (the ODFs of the paper: 328 intervals x 12 steps), count then gather.
+// k_odf_gather: ODFs of intervals of at most 65,536 points with at most 12 steps (the ODFs of
+// the paper: 328 intervals x 12 steps), count then gather; arithmetic or geometric means.
 //
 // Pass 1 (HBM) counts the values of each 14-bit prefix of the FP32 pattern (bits 30..17: the
 // exponent and six mantissa bits, 64 bins per octave) with one shared-memory add per value and
@@ -725,7 +725,8 @@ __global__ void __launch_bounds__(kOdfThreads, ODF_MINB) k_odf(const float* __re
 // two-sums (FP64 adds run at 1/64 of the FP32 rate on this part), then converted to FP64.  An
 // interval whose target bins hold more values than the candidate list, or that is longer than
 // 65,536 points, gets kOdfRedo in its first output word and is recomputed by k_odf, which also
-// serves more steps and the geometric means.
+// serves more steps.  Geometric means (GEOM) add ln x in the same columns as exact 64-bit
+// fixed-point sums (ln_q30, as k_odf) and count the zeros; their step means follow k_odf's.
 constexpr int kGThreads = 512;
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGShift = 17;                              // bin = bits 30..17
@@ -752,6 +753,7 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float a) {
     hi = s;
 }
 
+template <bool GEOM>
 __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __restrict__ kappa, int64_t N, int K,
                                                              const int64_t* __restrict__ bounds, int n_steps,
                                                              const double* __restrict__ cw,
@@ -769,6 +771,10 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
     __shared__ int s_cb[kGMaxSteps];      // values below the order statistic
     __shared__ double s_sb[kGMaxSteps];   // sum of its slot's values below it
     __shared__ double s_G[kGGaps], s_T[kGMaxSteps], s_P[kGMaxSteps + 1];
+    // geometric means: exact sums of ln x in units of 2^-30 (ln_q30), and the zero count
+    __shared__ long long s_G64[GEOM ? kGGaps : 1], s_T64[GEOM ? kGMaxSteps : 1], s_sb64[GEOM ? kGMaxSteps : 1];
+    __shared__ long long s_P64[GEOM ? kGMaxSteps + 1 : 1];
+    __shared__ int s_zero;
     __shared__ int s_wsum[kGWarps];
     __shared__ int s_nslots;
 
@@ -789,6 +795,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
 
     // u = c_s n as one rounded FP64 product, as in k_odf and the oracle
     if (tid < nt) s_kt[tid] = (int)floor(__dmul_rn(cw[tid + 1], (double)n));
+    if (tid == 0) s_zero = 0;
     for (int i = tid; i < kGBins / 4; i += kGThreads) reinterpret_cast<uint4*>(cnt)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
@@ -947,6 +954,8 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
     {
         float* colA = col + warp * (kGGaps * 32) + lane;
         float* colB = colA + kGColWords;
+        long long* colL = reinterpret_cast<long long*>(col) + warp * (kGGaps * 32) + lane;
+        int zeros = 0;
         auto to_cand = [&](unsigned bits) {
             const int pos = atomicAdd(&s_ccur[tbl[bits >> kGShift] & 0x7fu], 1);
             cand[pos] = bits;   // inside the slot's region: its size is the bin's count
@@ -971,14 +980,24 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
                     cd[4 * u + c] = ok ? tbl[bits >> kGShift] : 0xffu;
                 }
             }
+            if constexpr (!GEOM) {
 #pragma unroll
-            for (int e = 0; e < 4 * kGU; e += 2) {
-                const unsigned ca = cd[e], cb = cd[e + 1];
-                float a = 0.f, b = 0.f;
-                if (ca < (unsigned)kGGaps) a = colA[ca * 32];
-                if (cb < (unsigned)kGGaps) b = colB[cb * 32];
-                if (ca < (unsigned)kGGaps) colA[ca * 32] = a + v[e];
-                if (cb < (unsigned)kGGaps) colB[cb * 32] = b + v[e + 1];
+                for (int e = 0; e < 4 * kGU; e += 2) {
+                    const unsigned ca = cd[e], cb = cd[e + 1];
+                    float a = 0.f, b = 0.f;
+                    if (ca < (unsigned)kGGaps) a = colA[ca * 32];
+                    if (cb < (unsigned)kGGaps) b = colB[cb * 32];
+                    if (ca < (unsigned)kGGaps) colA[ca * 32] = a + v[e];
+                    if (cb < (unsigned)kGGaps) colB[cb * 32] = b + v[e + 1];
+                }
+            } else {
+                // ln x of the positive values in fixed point (exact 64-bit sums); zeros counted
+#pragma unroll
+                for (int e = 0; e < 4 * kGU; ++e) {
+                    const unsigned bits = __float_as_uint(v[e]);
+                    if (cd[e] != 0xffu && bits == 0u) ++zeros;
+                    if (cd[e] < (unsigned)kGGaps && bits != 0u) colL[cd[e] * 32] += ln_q30(bits);
+                }
             }
             unsigned cm = 0u;
 #pragma unroll
@@ -994,17 +1013,34 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
         auto one = [&](unsigned bits) {
             bits &= 0x7fffffffu;
             const unsigned code = tbl[bits >> kGShift];
-            if (code < (unsigned)kGGaps) colA[code * 32] += __uint_as_float(bits);
-            else to_cand(bits);
+            if (GEOM && bits == 0u) ++zeros;
+            if (code < (unsigned)kGGaps) {
+                if constexpr (!GEOM) colA[code * 32] += __uint_as_float(bits);
+                else if (bits != 0u) colL[code * 32] += ln_q30(bits);
+            } else {
+                to_cand(bits);
+            }
         };
         if (tid < head) one(__float_as_uint(__ldg(x + tid)));
         if (tid < n - tail0) one(__float_as_uint(__ldg(x + tail0 + tid)));
+        if (GEOM) {
+            zeros = __reduce_add_sync(kFull, zeros);
+            if (lane == 0 && zeros) atomicAdd(&s_zero, zeros);
+        }
     }
     __syncthreads();
 
     // ---- gap sums (one warp per gap): FP32 two-sums over the 32 columns of a lane, then over
     // the lanes, then FP64
-    if (warp <= ns) {
+    if (GEOM && warp <= ns) {
+        const long long* cl = reinterpret_cast<const long long*>(col);
+        long long sg = 0;
+        for (int v = 0; v < kGWarps; ++v) sg += cl[v * (kGGaps * 32) + warp * 32 + lane];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) sg += __shfl_down_sync(kFull, sg, d);
+        if (lane == 0) s_G64[warp] = sg;
+    }
+    if (!GEOM && warp <= ns) {
         float hi = 0.f, lo = 0.f;
 #pragma unroll 4
         for (int v = 0; v < kGBanks * kGWarps; ++v) two_sum_add(hi, lo, col[v * (kGGaps * 32) + warp * 32 + lane]);
@@ -1033,6 +1069,16 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) ts += __shfl_down_sync(kFull, ts, d);
         if (lane == 0) s_T[j] = ldexp((double)ts, eff - 150);
+        if (GEOM) {
+            long long tl = 0;
+            for (int i = c0 + lane; i < c1; i += 32) {
+                const unsigned c = cand[i];
+                if (c) tl += ln_q30(c);
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) tl += __shfl_down_sync(kFull, tl, d);
+            if (lane == 0) s_T64[j] = tl;
+        }
         for (int t = 0; t < nt; ++t) {
             if (s_tslot[t] != j) continue;   // uniform over the warp
             const int r = s_kt[t] - s_slt[j];   // rank inside the bin (below its count)
@@ -1107,6 +1153,16 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) sb += __shfl_down_sync(kFull, sb, d);
+            if (GEOM) {
+                long long sl = 0;
+                for (int i = c0 + lane; i < c1; i += 32) {
+                    const unsigned c = cand[i];
+                    if (c && c < theta) sl += ln_q30(c);
+                }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) sl += __shfl_down_sync(kFull, sl, d);
+                if (lane == 0) s_sb64[t] = sl;
+            }
             if (lane == 0) {
                 s_theta[t] = theta;
                 s_cb[t] = s_slt[j] + cA + cB;
@@ -1117,6 +1173,40 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
     }
     __syncthreads();
 
+    if constexpr (GEOM) {
+        // ---- geometric step means: G(u) = sum_{0<x<theta} ln x + (u - #{x<theta}) ln theta (the
+        // ln sums exact in units of 2^-30, scanned over the slots in 64-bit integers); a sub-bin
+        // whose rank range starts among the zeros has geometric mean 0, as in k_odf
+        if (warp == 0) {
+            const long long gj = lane <= ns ? s_G64[lane] : 0;
+            const long long v = gj + (lane < ns ? s_T64[lane] : 0);
+            long long inc = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= d) inc += y;
+            }
+            if (lane < ns) s_P64[lane] = inc - v + gj;
+            if (lane == ns) s_P64[ns] = inc;
+        }
+        __syncthreads();
+        if (tid < n_steps) {
+            auto G = [&](int bidx, double u) -> double {
+                if (bidx == 0) return 0.0;
+                if (bidx == n_steps || s_kt[bidx - 1] >= n) return (double)s_P64[ns] * 0x1p-30;
+                const int t = bidx - 1;
+                const double frac = u - (double)s_cb[t];
+                return (double)(s_P64[s_tslot[t]] + s_sb64[t]) * 0x1p-30 +
+                       (frac != 0.0 ? frac * ln_f32_bits(s_theta[t]) : 0.0);
+            };
+            const double a = __dmul_rn(cw[tid], (double)n);
+            const double b = __dmul_rn(cw[tid + 1], (double)n);
+            double r = 0.0;
+            if (!(a < (double)s_zero)) r = exp((G(tid + 1, b) - G(tid, a)) / (w[tid] * (double)n));
+            o[tid] = r;
+        }
+        return;
+    }
     // ---- step means: S(u) = (sum below theta) + (u - #below) theta at each boundary; s_P[j] is
     // the sum of everything below slot j's bin (an FP64 scan over the slots in warp 0), s_P[ns]
     // the total
@@ -1201,7 +1291,9 @@ int odf_setup() {
         err[dev] = cudaFuncSetAttribute(k_odf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)odf_smem_bytes(kMaxSteps));
         if (err[dev] == cudaSuccess)
-            err[dev] = cudaFuncSetAttribute(k_odf_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+            err[dev] = cudaFuncSetAttribute(k_odf_gather<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+        if (err[dev] == cudaSuccess)
+            err[dev] = cudaFuncSetAttribute(k_odf_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
     });
     if (err[dev] != cudaSuccess)
         return fail(MPSA_ECUDA, "build_odf: cudaFuncSetAttribute: %s", cudaGetErrorString(err[dev]));
@@ -1212,12 +1304,15 @@ int odf_launch(const float* kappa, int n_rows, int64_t N, int K, const int64_t* 
                const double* d_cw, const double* d_w, double* d_out, int mean_kind, cudaStream_t st) {
     int r;
     if ((r = odf_setup())) return r;
-    // arithmetic means with at most 12 steps: count then gather, and the exact multi-select
-    // only for the intervals the gather leaves (too long, or too many candidates); otherwise the
-    // multi-select for every interval
-    const bool gather = mean_kind == MPSA_MEAN_ARITH && n_steps <= kGMaxSteps;
+    // at most 12 steps: count then gather, and the exact multi-select only for the intervals the
+    // gather leaves (too long, or too many candidates); otherwise the multi-select for every
+    // interval
+    const bool gather = n_steps <= kGMaxSteps;
     if (gather) {
-        k_odf_gather<<<dim3(K, n_rows), kGThreads, kGSmem, st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w, d_out);
+        if (mean_kind == MPSA_MEAN_GEOM)
+            k_odf_gather<true><<<dim3(K, n_rows), kGThreads, kGSmem, st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w, d_out);
+        else
+            k_odf_gather<false><<<dim3(K, n_rows), kGThreads, kGSmem, st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w, d_out);
         MPSA_CUDA_TRY(cudaGetLastError());
     }
     k_odf<<<dim3(K, n_rows), kOdfThreads, odf_smem_bytes(n_steps), st>>>(kappa, N, K, d_bounds, n_steps, d_cw, d_w,

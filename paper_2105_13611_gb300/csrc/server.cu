@@ -4,7 +4,11 @@
 // wait in a FIFO queue; the worker admits the oldest one as soon as a stream slot
 // is free and its estimated device memory fits the HBM budget, so requests that
 // arrive while others run are started without waiting for the running ones, and
-// their kernels overlap on the device (one CUDA stream per slot).  Each request's
+// their kernels overlap on the device (one CUDA stream per slot).  Spectrum requests
+// (tens of milliseconds) run on a stream of the device's highest priority and ODF
+// requests (seconds, thousands of CTAs per launch) on one of the lowest, so that the
+// block scheduler starts a spectrum's CTAs as soon as running ones retire instead of after
+// every queued CTA of an ODF request (no preemption: a running CTA finishes).  Each request's
 // work is the same sequence of kernels as the direct entry points: populations,
 // synthesis in chunks of rows (bounded scratch), then the formal solution or the
 // ODF, and a copy of the result to a pinned staging buffer.  Completion is
@@ -53,12 +57,19 @@ struct Req {
     size_t out_bytes = 0, kc_bytes = 0, est = 0;
     // runtime
     int slot = -1;
+    cudaStream_t st = nullptr;   // the slot's stream of this request's priority
+    // ODF requests: dispatched one chunk of rows at a time; device buffers kept across chunks
+    int next_row = 0;
+    int* dsel = nullptr;
+    float *kap = nullptr, *kc = nullptr;
+    int64_t* db = nullptr;
+    double *dcw = nullptr, *dw = nullptr, *dout = nullptr;
     cudaEvent_t ev = nullptr;
     Clock::time_point t_submit, t_start, t_done;
 };
 
 struct Slot {
-    cudaStream_t st = nullptr;
+    cudaStream_t st_hi = nullptr, st_lo = nullptr;   // highest and lowest priority
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
     Req* r = nullptr;
@@ -94,7 +105,7 @@ size_t synth_scratch_bytes(const mpsa_ctx* c, int rows, int N) {
 
 int launch_spectrum(mpsa_server* s, Req* r, Slot& sl) {
     mpsa_ctx* c = s->ctx;
-    cudaStream_t st = sl.st;
+    cudaStream_t st = r->st;
     const int D = (int)r->m.size(), N = r->N, n_mu = (int)r->mu.size(), ne = c->n_el;
     Scratch sc(st, s->ctx->pool);
     double *dT, *dP, *dab, *dpop;
@@ -132,34 +143,65 @@ int launch_spectrum(mpsa_server* s, Req* r, Slot& sl) {
     return MPSA_OK;
 }
 
-int launch_odf(mpsa_server* s, Req* r, Slot& sl) {
-    mpsa_ctx* c = s->ctx;
-    cudaStream_t st = sl.st;
+// ODF requests run one chunk of rows per dispatch: launch_odf allocates the request's
+// buffers and copies its inputs, odf_chunk enqueues the next chunk (synthesis + ODF) and,
+// after the last, the copies to the staging buffer and the frees.  The worker dispatches the
+// next chunk when the previous one's event has completed, so at most one chunk of a large
+// request is queued on the device at any time and other requests' kernels interleave.
+template <class T>
+int pool_alloc(mpsa_server* s, T** p, size_t n, cudaStream_t st) {
+    const cudaError_t e = cudaMallocFromPoolAsync((void**)p, (n ? n : 1) * sizeof(T), s->ctx->pool, st);
+    return e == cudaSuccess ? MPSA_OK
+                            : fail(e == cudaErrorMemoryAllocation ? MPSA_ENOMEM : MPSA_ECUDA,
+                                   "mpsa_server: cudaMallocFromPoolAsync(%zu bytes): %s", n * sizeof(T),
+                                   cudaGetErrorString(e));
+}
+
+void odf_free(Req* r) {
+    void* ps[7] = {r->dsel, r->kap, r->kc, r->db, r->dcw, r->dw, r->dout};
+    for (void* p : ps)
+        if (p) cudaFreeAsync(p, r->st);
+    r->dsel = nullptr, r->kap = r->kc = nullptr, r->db = nullptr, r->dcw = r->dw = r->dout = nullptr;
+}
+
+int launch_odf(mpsa_server* s, Req* r, Slot&) {
+    cudaStream_t st = r->st;
     const int n_sel = (int)r->sel.size(), N = r->N, K = (int)r->bounds.size() - 1, ns = (int)r->widths.size();
     const int chunk = std::min(s->rows_per_chunk, n_sel);
-    Scratch sc(st, s->ctx->pool);
-    int* dsel;
-    float *kap, *kc;
-    int64_t* db;
-    double *dcw, *dw, *dout;
     int rc;
-    if ((rc = sc.alloc(&dsel, n_sel)) || (rc = sc.alloc(&kap, (size_t)chunk * N)) || (rc = sc.alloc(&kc, n_sel)) ||
-        (rc = sc.alloc(&db, K + 1)) || (rc = sc.alloc(&dcw, ns + 1)) || (rc = sc.alloc(&dw, ns)) ||
-        (rc = sc.alloc(&dout, (size_t)n_sel * K * ns)))
+    if ((rc = pool_alloc(s, &r->dsel, n_sel, st)) || (rc = pool_alloc(s, &r->kap, (size_t)chunk * N, st)) ||
+        (rc = pool_alloc(s, &r->kc, n_sel, st)) || (rc = pool_alloc(s, &r->db, K + 1, st)) ||
+        (rc = pool_alloc(s, &r->dcw, ns + 1, st)) || (rc = pool_alloc(s, &r->dw, ns, st)) ||
+        (rc = pool_alloc(s, &r->dout, (size_t)n_sel * K * ns, st))) {
+        odf_free(r);
         return rc;
-    MPSA_CUDA_TRY(cudaMemcpyAsync(dsel, r->sel.data(), n_sel * sizeof(int), cudaMemcpyHostToDevice, st));
-    MPSA_CUDA_TRY(cudaMemcpyAsync(db, r->bounds.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    MPSA_CUDA_TRY(cudaMemcpyAsync(dcw, r->cw.data(), (ns + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-    MPSA_CUDA_TRY(cudaMemcpyAsync(dw, r->widths.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
-    for (int off = 0; off < n_sel; off += chunk) {
-        const int nrow = std::min(chunk, n_sel - off);
-        if ((rc = synth_rows(c, c->d_pop, nrow, dsel + off, r->grid.lambda0_nm, r->grid.R, N, kap, kc + off, nullptr,
-                             nullptr, st)))
-            return rc;
-        if ((rc = odf_launch(kap, nrow, N, K, db, ns, dcw, dw, dout + (size_t)off * K * ns, r->mean_kind, st))) return rc;
     }
-    MPSA_CUDA_TRY(cudaMemcpyAsync(sl.pinned, dout, r->out_bytes, cudaMemcpyDeviceToHost, st));
-    MPSA_CUDA_TRY(cudaMemcpyAsync((char*)sl.pinned + r->out_bytes, kc, r->kc_bytes, cudaMemcpyDeviceToHost, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(r->dsel, r->sel.data(), n_sel * sizeof(int), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(r->db, r->bounds.data(), (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(r->dcw, r->cw.data(), (ns + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+    MPSA_CUDA_TRY(cudaMemcpyAsync(r->dw, r->widths.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    r->next_row = 0;
+    return MPSA_OK;
+}
+
+int odf_chunk(mpsa_server* s, Req* r, Slot& sl) {
+    mpsa_ctx* c = s->ctx;
+    cudaStream_t st = r->st;
+    const int n_sel = (int)r->sel.size(), N = r->N, K = (int)r->bounds.size() - 1, ns = (int)r->widths.size();
+    const int off = r->next_row, nrow = std::min(std::min(s->rows_per_chunk, n_sel), n_sel - off);
+    int rc;
+    if ((rc = synth_rows(c, c->d_pop, nrow, r->dsel + off, r->grid.lambda0_nm, r->grid.R, N, r->kap, r->kc + off,
+                         nullptr, nullptr, st)))
+        return rc;
+    if ((rc = odf_launch(r->kap, nrow, N, K, r->db, ns, r->dcw, r->dw, r->dout + (size_t)off * K * ns, r->mean_kind,
+                         st)))
+        return rc;
+    r->next_row = off + nrow;
+    if (r->next_row == n_sel) {
+        MPSA_CUDA_TRY(cudaMemcpyAsync(sl.pinned, r->dout, r->out_bytes, cudaMemcpyDeviceToHost, st));
+        MPSA_CUDA_TRY(cudaMemcpyAsync((char*)sl.pinned + r->out_bytes, r->kc, r->kc_bytes, cudaMemcpyDeviceToHost, st));
+        odf_free(r);
+    }
     return MPSA_OK;
 }
 
@@ -170,10 +212,26 @@ int launch(mpsa_server* s, Req* r, Slot& sl) {
         MPSA_CUDA_TRY(cudaHostAlloc(&sl.pinned, need, cudaHostAllocDefault));
         sl.pinned_bytes = need;
     }
+    r->st = r->kind == MPSA_REQ_SPECTRUM ? sl.st_hi : sl.st_lo;
     int rc = r->kind == MPSA_REQ_SPECTRUM ? launch_spectrum(s, r, sl) : launch_odf(s, r, sl);
-    if (rc != MPSA_OK) return rc;
+    if (rc == MPSA_OK && r->kind != MPSA_REQ_SPECTRUM) rc = odf_chunk(s, r, sl);
+    if (rc != MPSA_OK) {
+        if (r->kind != MPSA_REQ_SPECTRUM) odf_free(r);
+        return rc;
+    }
     MPSA_CUDA_TRY(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
-    MPSA_CUDA_TRY(cudaEventRecord(r->ev, sl.st));
+    MPSA_CUDA_TRY(cudaEventRecord(r->ev, r->st));
+    return MPSA_OK;
+}
+
+// The next chunk of a running ODF request (its previous chunk has completed).
+int continue_odf(mpsa_server* s, Req* r, Slot& sl) {
+    int rc = odf_chunk(s, r, sl);
+    if (rc != MPSA_OK) {
+        odf_free(r);
+        return rc;
+    }
+    MPSA_CUDA_TRY(cudaEventRecord(r->ev, r->st));
     return MPSA_OK;
 }
 
@@ -202,7 +260,19 @@ void worker_loop(mpsa_server* s) {
         for (auto& sl : s->slots) {
             if (!sl.r) continue;
             const cudaError_t q = cudaEventQuery(sl.r->ev);
-            if (q == cudaSuccess) {
+            if (q == cudaSuccess && sl.r->kind != MPSA_REQ_SPECTRUM && sl.r->next_row < (int)sl.r->sel.size()) {
+                Req* r = sl.r;
+                lk.unlock();
+                const int rc = continue_odf(s, r, sl);
+                lk.lock();
+                if (rc != MPSA_OK) {
+                    r->err = mpsa_last_error();
+                    cudaStreamSynchronize(r->st);
+                    finish(s, r, sl, rc);
+                } else {
+                    running = true;
+                }
+            } else if (q == cudaSuccess) {
                 finish(s, sl.r, sl, 2);
             } else if (q != cudaErrorNotReady) {
                 cudaGetLastError();
@@ -234,7 +304,7 @@ void worker_loop(mpsa_server* s) {
             lk.lock();
             if (rc != MPSA_OK) {
                 r->err = mpsa_last_error();
-                cudaStreamSynchronize(free_slot->st);
+                if (r->st) cudaStreamSynchronize(r->st);
                 finish(s, r, *free_slot, rc);
                 s->cv_done.notify_all();
             } else {
@@ -266,11 +336,16 @@ int mpsa_server_create(mpsa_server** out, mpsa_ctx* ctx, size_t hbm_budget_bytes
     s->budget = hbm_budget_bytes;
     s->rows_per_chunk = rows_per_chunk;
     s->slots.resize(max_inflight);
+    int least = 0, greatest = 0;
+    MPSA_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
     for (auto& sl : s->slots) {
-        cudaError_t e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+        cudaError_t e = cudaStreamCreateWithPriority(&sl.st_hi, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.st_lo, cudaStreamNonBlocking, least);
         if (e != cudaSuccess) {
-            for (auto& q : s->slots)
-                if (q.st) cudaStreamDestroy(q.st);
+            for (auto& q : s->slots) {
+                if (q.st_hi) cudaStreamDestroy(q.st_hi);
+                if (q.st_lo) cudaStreamDestroy(q.st_lo);
+            }
             delete s;
             return fail(MPSA_ECUDA, "mpsa_server_create: %s", cudaGetErrorString(e));
         }
@@ -431,7 +506,8 @@ void mpsa_server_destroy(mpsa_server* s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     for (auto& sl : s->slots) {
-        if (sl.st) cudaStreamSynchronize(sl.st), cudaStreamDestroy(sl.st);
+        if (sl.st_hi) cudaStreamSynchronize(sl.st_hi), cudaStreamDestroy(sl.st_hi);
+        if (sl.st_lo) cudaStreamSynchronize(sl.st_lo), cudaStreamDestroy(sl.st_lo);
         if (sl.pinned) cudaFreeHost(sl.pinned);
     }
     for (auto& kv : s->reqs) delete kv.second;

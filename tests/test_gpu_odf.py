@@ -153,7 +153,7 @@ def test_many_ragged_intervals():
 
 
 def test_gather_and_multiselect_paths():
-    # arithmetic means with at most 12 steps take the count-then-gather kernel, which leaves an
+    # means with at most 12 steps take the count-then-gather kernel, which leaves an
     # interval to the exact multi-select when it is longer than 65,536 points or when its target
     # bins hold more than 16,384 values; mixed in one call, every interval must match the oracle
     rng = np.random.default_rng(29)
@@ -166,6 +166,11 @@ def test_gather_and_multiselect_paths():
     x = np.concatenate(parts)
     b = np.r_[0, np.cumsum([len(p) for p in parts])]
     check(x, b, W12)
+    check(x, b, W12, mean="geom")
+    # zeros in a gathered interval: a boundary bin holding the zeros, and sub-bins among them
+    z = np.r_[np.zeros(3000), rng.lognormal(0, 2, 27_000)]
+    check(z, [0, len(z)], W12, mean="geom")
+    check(z, [0, len(z)], W12)
     # 13 steps: every interval through the multi-select
     w13 = np.r_[np.full(9, 0.1), 0.04, 0.03, 0.02, 0.01]
     check(x, b, w13)
