@@ -155,22 +155,25 @@ def test_many_ragged_intervals():
 def test_gather_and_multiselect_paths():
     # means with at most 12 steps take the count-then-gather kernel, which leaves an
     # interval to the exact multi-select when it is longer than 65,536 points or when its target
-    # bins hold more than 16,384 values; mixed in one call, every interval must match the oracle
+    # bins hold more than 8,192 values; mixed in one call, every interval must match the oracle
     rng = np.random.default_rng(29)
     parts = [rng.lognormal(0, 4, 65_536),                  # longest gathered interval
              rng.lognormal(0, 4, 65_537),                  # one point longer: multi-select
              np.full(20_000, 3.25),                        # one bin, 20,000 candidates: multi-select
-             np.full(16_384, 7.5),                         # one bin, exactly the candidate capacity
+             np.full(8_192, 7.5),                          # one bin, exactly the candidate capacity
+             np.full(8_193, 9.5),                          # one value over it: multi-select
              1.0 + 1e-3 * rng.random(30_000),              # a few bins, most values are candidates
              rng.lognormal(-20, 8, 4097)]
     x = np.concatenate(parts)
     b = np.r_[0, np.cumsum([len(p) for p in parts])]
     check(x, b, W12)
     check(x, b, W12, mean="geom")
-    # zeros in a gathered interval: a boundary bin holding the zeros, and sub-bins among them
-    z = np.r_[np.zeros(3000), rng.lognormal(0, 2, 27_000)]
-    check(z, [0, len(z)], W12, mean="geom")
-    check(z, [0, len(z)], W12)
+    # zeros in a gathered interval: all below the first boundary (a gap of zeros), and a
+    # boundary among them (the zeros are candidates of a boundary bin)
+    for nz in (3000, 5000):
+        z = np.r_[np.zeros(nz), rng.lognormal(0, 2, 30_000 - nz)]
+        check(z, [0, len(z)], W12, mean="geom")
+        check(z, [0, len(z)], W12)
     # 13 steps: every interval through the multi-select
     w13 = np.r_[np.full(9, 0.1), 0.04, 0.03, 0.02, 0.01]
     check(x, b, w13)
