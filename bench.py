@@ -368,7 +368,7 @@ def native_arm(args):
 
         e2e_step()
         barrier()
-        n_e2e = min(args.steps, 2)
+        n_e2e = args.steps
         t0 = time.perf_counter()
         ev_e2e = 0
         for _ in range(n_e2e):
