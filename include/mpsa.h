@@ -117,10 +117,12 @@ typedef struct {
  *     species s belongs to element species_element[s] (index into the element
  *     table of set_atmosphere_grid) in stage species_stage[s] (0 = I, 1 = II, ...,
  *     4 = V; stages above II need set_atmosphere_grid_eos).
- *   lines (host): the list, ascending in lambda_nm (MPSA_EINVAL otherwise).
+ *   lines (host): the list in any order.  The kernels need it ascending in
+ *     lambda_nm: a list that is not is sorted (stably, lines of equal lambda
+ *     keep their order) into a host copy before the upload.
  * Replaces any previously loaded list.  Synchronises the device on return.
- * Errors: MPSA_EINVAL (n_lines < 1, non-finite or unsorted lambda, species out
- * of range), MPSA_ENOMEM, MPSA_ECUDA.
+ * Errors: MPSA_EINVAL (n_lines < 1, non-finite or non-positive lambda, species
+ * out of range, non-finite line parameters), MPSA_ENOMEM, MPSA_ECUDA.
  */
 int load_linelist(mpsa_ctx* ctx, int32_t n_species, const int32_t* species_element,
                   const int32_t* species_stage, const mpsa_lines* lines);

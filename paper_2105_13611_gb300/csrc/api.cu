@@ -236,24 +236,54 @@ int load_linelist(mpsa_ctx* c, int32_t n_species, const int32_t* sp_el, const in
     for (int s = 0; s < n_species; ++s)
         if (sp_el[s] < 0 || sp_stage[s] < 0 || sp_stage[s] >= kMaxStages)
             return fail(MPSA_EINVAL, "load_linelist: species %d has element %d stage %d", s, sp_el[s], sp_stage[s]);
+    bool ascending = true;
     for (int64_t i = 0; i < L; ++i) {
         const double lam = ln->lambda_nm[i];
         if (!(lam > 0) || !isfinite(lam)) return fail(MPSA_EINVAL, "load_linelist: lambda[%lld] = %g", (long long)i, lam);
-        if (i > 0 && lam < ln->lambda_nm[i - 1])
-            return fail(MPSA_EINVAL, "load_linelist: lambda not ascending at %lld", (long long)i);
+        if (i > 0 && lam < ln->lambda_nm[i - 1]) ascending = false;
         if (ln->species[i] < 0 || ln->species[i] >= n_species)
             return fail(MPSA_EINVAL, "load_linelist: species[%lld] = %d", (long long)i, ln->species[i]);
         if (!isfinite(ln->log_gf[i]) || !isfinite(ln->E_eV[i]) || !isfinite(ln->log_gR[i]) ||
             !isfinite(ln->log_gS[i]) || !isfinite(ln->log_gW[i]))
             return fail(MPSA_EINVAL, "load_linelist: non-finite parameter of line %lld", (long long)i);
     }
+    // the kernels need the list ascending in lambda (tiles find their lines by binary search):
+    // a list in any other order is sorted here, stably, into a host copy
+    mpsa_lines src = *ln;
+    std::vector<double> s_lam;
+    std::vector<float> s_gf, s_E, s_gR, s_gS, s_gW;
+    std::vector<int32_t> s_sp;
+    if (!ascending) {
+        std::vector<int64_t> perm((size_t)L);
+        for (int64_t i = 0; i < L; ++i) perm[(size_t)i] = i;
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](int64_t a, int64_t b) { return ln->lambda_nm[a] < ln->lambda_nm[b]; });
+        auto gather = [&](auto& dst, const auto* from) {
+            dst.resize((size_t)L);
+            for (int64_t i = 0; i < L; ++i) dst[(size_t)i] = from[perm[(size_t)i]];
+        };
+        gather(s_lam, ln->lambda_nm);
+        gather(s_gf, ln->log_gf);
+        gather(s_E, ln->E_eV);
+        gather(s_sp, ln->species);
+        gather(s_gR, ln->log_gR);
+        gather(s_gS, ln->log_gS);
+        gather(s_gW, ln->log_gW);
+        src.lambda_nm = s_lam.data();
+        src.log_gf = s_gf.data();
+        src.E_eV = s_E.data();
+        src.species = s_sp.data();
+        src.log_gR = s_gR.data();
+        src.log_gS = s_gS.data();
+        src.log_gW = s_gW.data();
+    }
     MPSA_CUDA_TRY(cudaSetDevice(c->device));
     int rc;
     if ((rc = upload(&c->d_sp_el, sp_el, n_species)) || (rc = upload(&c->d_sp_stage, sp_stage, n_species)) ||
-        (rc = upload(&c->d_lam, ln->lambda_nm, L)) || (rc = upload(&c->d_loggf, ln->log_gf, L)) ||
-        (rc = upload(&c->d_E, ln->E_eV, L)) || (rc = upload(&c->d_lgR, ln->log_gR, L)) ||
-        (rc = upload(&c->d_lgS, ln->log_gS, L)) || (rc = upload(&c->d_lgW, ln->log_gW, L)) ||
-        (rc = upload(&c->d_species, ln->species, L))) {
+        (rc = upload(&c->d_lam, src.lambda_nm, L)) || (rc = upload(&c->d_loggf, src.log_gf, L)) ||
+        (rc = upload(&c->d_E, src.E_eV, L)) || (rc = upload(&c->d_lgR, src.log_gR, L)) ||
+        (rc = upload(&c->d_lgS, src.log_gS, L)) || (rc = upload(&c->d_lgW, src.log_gW, L)) ||
+        (rc = upload(&c->d_species, src.species, L))) {
         c->L = 0;
         return rc;
     }

@@ -256,3 +256,20 @@ def test_single_point_and_single_line():
         bad, _, _ = opacity_violations(kg[s], k, pl.kappa_c, slack)
         assert len(bad) == 0
     assert np.all(np.isfinite(cont.cpu().numpy())) and float(cont.min()) > 0
+
+
+def test_unsorted_list_is_sorted_by_the_library():
+    # load_linelist takes a list in any order and sorts a copy by wavelength (stably): the
+    # opacity of a shuffled list equals that of the sorted one bit for bit, and the oracle's
+    w = wl.config_tiny(n_lines=400, lam=(300.0, 303.1), seed=8)
+    ctx, L = gpu_context(w)
+    sel = np.arange(len(w.T))
+    kg, kcg, evg = gpu_synth(ctx, w, sel)
+    perm = np.random.default_rng(73).permutation(len(L))
+    ctx2, _ = gpu_context(w, lines=L.subset(perm))
+    kg2, kcg2, evg2 = gpu_synth(ctx2, w, sel)
+    assert np.array_equal(kg, kg2) and np.array_equal(kcg, kcg2) and np.array_equal(evg, evg2)
+    for s in sel:
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        bad, _, _ = opacity_violations(kg2[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0
