@@ -424,10 +424,11 @@ void mpsa_batch_destroy(mpsa_batch* b);
  * Requests wait in FIFO order; the oldest is started as soon as one of
  * max_inflight stream slots is free and its estimated device memory fits the
  * budget, so requests arriving while others run are admitted without waiting
- * for them and their kernels overlap on the device.  Spectrum requests run on
- * streams of the device's highest priority and ODF requests on its lowest, so
- * the block scheduler starts a spectrum's CTAs ahead of an ODF request's
- * queued ones (running CTAs are not preempted).  Each request runs exactly
+ * for them and their kernels overlap on the device.  Spectrum requests run
+ * whole on streams of the device's highest priority.  ODF requests run on its
+ * lowest, one chunk of rows at a time (the next when the previous completes), so
+ * a spectrum waits behind at most one chunk (running CTAs are not preempted).
+ * Each request runs exactly
  * the kernels of the direct entry points (synthesis in chunks of
  * rows_per_chunk rows to bound scratch), so its result does not depend on what
  * else is in flight.

@@ -4,16 +4,20 @@
 // wait in a FIFO queue; the worker admits the oldest one as soon as a stream slot
 // is free and its estimated device memory fits the HBM budget, so requests that
 // arrive while others run are started without waiting for the running ones, and
-// their kernels overlap on the device (one CUDA stream per slot).  Spectrum requests
-// (tens of milliseconds) run on a stream of the device's highest priority and ODF
-// requests (seconds, thousands of CTAs per launch) on one of the lowest, so that the
-// block scheduler starts a spectrum's CTAs as soon as running ones retire instead of after
-// every queued CTA of an ODF request (no preemption: a running CTA finishes).  Each request's
-// work is the same sequence of kernels as the direct entry points: populations,
-// synthesis in chunks of rows (bounded scratch), then the formal solution or the
-// ODF, and a copy of the result to a pinned staging buffer.  Completion is
-// detected by polling a CUDA event (no blocking wait on the device); the result is
-// copied to the caller's host buffer and the request's latency recorded.
+// their kernels overlap on the device (CUDA streams per slot).  Each request's work
+// is the same sequence of kernels as the direct entry points: populations, synthesis
+// in chunks of rows (bounded scratch), then the formal solution or the ODF, and a copy
+// of the result to a pinned staging buffer.  Completion is detected by polling a CUDA
+// event (no blocking wait on the device); the result is copied to the caller's host
+// buffer and the request's latency recorded.
+//
+// Small requests are kept from waiting behind large ones in two ways.  A spectrum
+// request (tens of milliseconds) is enqueued whole on a stream of the device's highest
+// priority; an ODF request (seconds of work in hundreds of chunks) is dispatched one
+// chunk of rows at a time on a stream of the lowest priority, the next chunk when the
+// previous one's event has completed.  So at most one chunk of an ODF request is queued
+// on the device, and the block scheduler starts a spectrum's CTAs ahead of that chunk's
+// queued ones (there is no preemption: running CTAs finish).
 #include <math.h>
 #include <string.h>
 
