@@ -948,9 +948,10 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
         reinterpret_cast<uint4*>(col)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
-    // ---- pass 2 (L2): gap columns and candidates.  All 16 codes of an iteration are read
-    // before any column is written, and the two banks take alternate values, so each lane's
-    // read-add-write steps form two independent chains.
+    // ---- pass 2 (L2): gap columns and candidates.  The loads of the next iteration are issued
+    // before the current one is processed (the pass waits on L2 latency); all 8 codes of an
+    // iteration are read before any column is written, and the two banks take alternate
+    // values, so each lane's read-add-write steps form two independent chains.
     {
         float* colA = col + warp * (kGGaps * 32) + lane;
         float* colB = colA + kGColWords;
@@ -960,17 +961,24 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
             const int pos = atomicAdd(&s_ccur[tbl[bits >> kGShift] & 0x7fu], 1);
             cand[pos] = bits;   // inside the slot's region: its size is the bin's count
         };
-        for (int i0 = 0; i0 < nv; i0 += kGU * kGThreads) {
-            float4 q[kGU];
+        constexpr int P2U = 2;
+        float4 q[P2U], qn[P2U];
+        auto load2 = [&](float4* dst, int j0) {
 #pragma unroll
-            for (int u = 0; u < kGU; ++u) {
-                const int i = i0 + u * kGThreads + tid;
-                q[u] = i < nv ? __ldcs(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < P2U; ++u) {
+                const int i = j0 + u * kGThreads + tid;
+                dst[u] = i < nv ? __ldcs(body + i) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            float v[4 * kGU];
-            unsigned cd[4 * kGU];
+        };
+        load2(q, 0);
 #pragma unroll
-            for (int u = 0; u < kGU; ++u) {
+        for (int u = 0; u < P2U; ++u) qn[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i0 = 0; i0 < nv; i0 += P2U * kGThreads) {
+            if (i0 + P2U * kGThreads < nv) load2(qn, i0 + P2U * kGThreads);
+            float v[4 * P2U];
+            unsigned cd[4 * P2U];
+#pragma unroll
+            for (int u = 0; u < P2U; ++u) {
                 const bool ok = i0 + u * kGThreads + tid < nv;
                 const float qq[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
@@ -982,7 +990,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
             }
             if constexpr (!GEOM) {
 #pragma unroll
-                for (int e = 0; e < 4 * kGU; e += 2) {
+                for (int e = 0; e < 4 * P2U; e += 2) {
                     const unsigned ca = cd[e], cb = cd[e + 1];
                     float a = 0.f, b = 0.f;
                     if (ca < (unsigned)kGGaps) a = colA[ca * 32];
@@ -993,7 +1001,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
             } else {
                 // ln x of the positive values in fixed point (exact 64-bit sums); zeros counted
 #pragma unroll
-                for (int e = 0; e < 4 * kGU; ++e) {
+                for (int e = 0; e < 4 * P2U; ++e) {
                     const unsigned bits = __float_as_uint(v[e]);
                     if (cd[e] != 0xffu && bits == 0u) ++zeros;
                     if (cd[e] < (unsigned)kGGaps && bits != 0u) colL[cd[e] * 32] += ln_q30(bits);
@@ -1001,7 +1009,7 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
             }
             unsigned cm = 0u;
 #pragma unroll
-            for (int e = 0; e < 4 * kGU; ++e)
+            for (int e = 0; e < 4 * P2U; ++e)
                 if (cd[e] >= 0x80u && cd[e] != 0xffu) cm |= 1u << e;
             while (cm) {   // rare: reload the value (an L1/L2 hit) rather than keep it
                 const int e = __ffs(cm) - 1;
@@ -1009,6 +1017,8 @@ __global__ void __launch_bounds__(kGThreads, 2) k_odf_gather(const float* __rest
                 const int i = i0 + (e >> 2) * kGThreads + tid;
                 to_cand(__float_as_uint(__ldg(x + head + 4 * i + (e & 3))) & 0x7fffffffu);
             }
+#pragma unroll
+            for (int u = 0; u < P2U; ++u) q[u] = qn[u];
         }
         auto one = [&](unsigned bits) {
             bits &= 0x7fffffffu;
