@@ -63,9 +63,13 @@ def parse():
                    help="comma-separated table rows (T index * 25 + P index) instead of the default batch")
     p.add_argument("--workload", choices=["table", "small"], default="table",
                    help="table: 5e6 lines, 9-10000 nm, 57x25 T-P grid; small: 20,000 lines, 300-400 nm, 4 points")
-    p.add_argument("--mode", choices=["step", "serve", "batch", "precision", "bins", "table"], default="step",
+    p.add_argument("--mode", choices=["step", "serve", "batch", "precision", "bins", "table", "spectrum"],
+                   default="step",
                    help="step: the throughput benchmark; serve: Poisson request stream through the server; "
-                        "batch: persistent graph-captured batch against the plain per-point path")
+                        "batch: persistent graph-captured batch against the plain per-point path; "
+                        "spectrum: one spectrum request (80 depths) on windows of several lengths")
+    p.add_argument("--spectrum-windows", type=str, default="1,10,100",
+                   help="window lengths [nm] of the spectrum mode, from 500 nm at R = 5e5")
     p.add_argument("--batch-rows", type=int, default=4, help="ODF rows (composition, T, P) in the batch sample")
     p.add_argument("--batch-windows", type=int, default=200, help="spectrum windows in the batch sample")
     p.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the latency stream")
@@ -658,6 +662,40 @@ def batch_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def spectrum_arm(args):
+    """One spectrum request of the serving workload's kind, timed alone: synth_spectrum over the
+    5e6-line table list for the solar grey atmosphere (80 depths, Teff 5772 K, log g 4.44) on
+    windows from 500 nm at R = 5e5 with 5 mu angles.  Each window: `warmup` untimed calls, then
+    `steps` calls, each timed from the host around the call with a synchronize on both sides."""
+    import torch
+    from paper_2105_13611_gb300 import binding
+    w = wl.config_table()
+    lines = w.lines()
+    se, ss = wl.species_table(w.n_metals)
+    ctx = binding.Context(0)
+    ctx.load_linelist(lines, se, ss)
+    ctx.set_atmosphere_grid(wl.elements(w.n_metals), w.T, w.P)
+    mus = [1.0, 0.8, 0.6, 0.4, 0.2]
+    m, T, P = wl.grey_atmosphere(80, 5772.0, 4.44)
+    res = []
+    for length in [float(x) for x in args.spectrum_windows.split(",") if x]:
+        g = wl.Grid(500.0, 500.0 + length, 5e5)
+        N = binding.grid_size(g.lam0_nm, g.lam1_nm, g.R)
+        I = torch.empty((len(mus), N), dtype=torch.float32, device="cuda")
+        ts = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.synth_spectrum(m, T, P, g, mus, I)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ts.append((time.perf_counter() - t0) * 1e3)
+        res.append({"window_nm": length, "N": N, "ms": ts, "ms_median": float(np.median(ts))})
+    ctx.close()
+    print(json.dumps({"mode": "spectrum", "metric": "ms per spectrum request (80 depths, 5 mu, 5e6 lines)",
+                      "windows": res, "data": "synthetic"}), flush=True)
+
+
 def bins_arm(args):
     """Module III through ODF tables (odf_intensity): emergent bin intensities of many 1D rays
     (grey atmospheres, 80 depths, 5 directions) from a seeded synthetic ODF table on the 57 x 25
@@ -985,6 +1023,9 @@ def main():
         return
     if args.mode == "serve":
         serve_arm(args)
+        return
+    if args.mode == "spectrum":
+        spectrum_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args)

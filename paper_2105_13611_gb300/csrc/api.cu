@@ -59,45 +59,68 @@ int upload(T** dst, const T* src, size_t n) {
 // is found by Newton steps in y kept inside a shrinking bracket (bisection where a step would
 // leave it), to a relative change of n_e below 1e-14.  The stage weights prod_{i<j} Phi_i / n_e
 // are formed in log space and scaled by their largest value, so no ratio overflows.
+//
+// One warp per row: lane l holds elements l and l + 32 (at most 64), and every sum over the
+// elements is a warp reduction whose result all lanes share, so the lanes take the same
+// Newton steps.
+constexpr int kPopElPerLane = 2;
+
+// sum over the warp, lane 0's result given to every lane (the same bits in all lanes)
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
 __global__ void k_populations(int rows, int n_points, int n_el, const double* __restrict__ el,
                               const double* __restrict__ abund, const double* __restrict__ T,
                               const double* __restrict__ P, double* __restrict__ pop) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
+    const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (r >= rows) return;   // the same for every lane of the warp
     const int comp = r / n_points, pt = r % n_points;
     const double t = T[pt], p = P[pt];
     const double kT = kKB * t;
     const double lsaha = 1.5 * log(2.0 * kPI * kME * kT / (kH * kH));
     const double x = log(t / 5040.0);
     double* row = pop + (size_t)r * pop_stride(n_el);
-    double eps_sum = 0.0;
-    for (int e = 0; e < n_el; ++e) eps_sum += pow(10.0, el[e * kElStride + kElLogEps] - 12.0) * abund[(size_t)comp * n_el + e];
-    double frac[64];
-    double lphi[64][kMaxStages - 1];   // ln Phi_{e,j}
-    double lU[64][kMaxStages];          // ln U_{e,j}
-    int ns[64];
-    for (int e = 0; e < n_el; ++e) {
+    double eps[kPopElPerLane];
+    double eps_part = 0.0;
+    for (int k = 0; k < kPopElPerLane; ++k) {
+        const int e = lane + 32 * k;
+        eps[k] = e < n_el ? pow(10.0, el[e * kElStride + kElLogEps] - 12.0) * abund[(size_t)comp * n_el + e] : 0.0;
+        eps_part += eps[k];
+    }
+    const double eps_sum = warp_sum(eps_part);
+    double frac[kPopElPerLane];
+    double lphi[kPopElPerLane][kMaxStages - 1];   // ln Phi_{e,j}
+    double lU[kPopElPerLane][kMaxStages];          // ln U_{e,j}
+    int ns[kPopElPerLane];
+    for (int k = 0; k < kPopElPerLane; ++k) {
+        const int e = lane + 32 * k;
+        ns[k] = 0;
+        frac[k] = 0.0;
+        if (e >= n_el) continue;
         const double* q = el + e * kElStride;
-        frac[e] = pow(10.0, q[kElLogEps] - 12.0) * abund[(size_t)comp * n_el + e] / eps_sum;
-        ns[e] = (int)q[kElStages];
-        for (int j = 0; j < ns[e]; ++j) {
+        frac[k] = eps[k] / eps_sum;
+        ns[k] = (int)q[kElStages];
+        for (int j = 0; j < ns[k]; ++j) {
             const double* c = q + kElLnU + 3 * j;
-            lU[e][j] = c[0] + x * (c[1] + x * c[2]);
+            lU[k][j] = c[0] + x * (c[1] + x * c[2]);
         }
-        for (int j = 0; j + 1 < ns[e]; ++j)
-            lphi[e][j] = 0.69314718055994530942 + lU[e][j + 1] - lU[e][j] + lsaha - q[kElChi + j] * kEV / kT;
+        for (int j = 0; j + 1 < ns[k]; ++j)
+            lphi[k][j] = 0.69314718055994530942 + lU[k][j + 1] - lU[k][j] + lsaha - q[kElChi + j] * kEV / kT;
     }
     const double n_tot = p / kT;
-    // stage weights of element e at y = ln n_e: w_j = exp(lp_j - max lp), lp_j = sum_{i<j} (ln Phi_i - y)
-    auto weights = [&](int e, double y, double* w) -> double {
+    // stage weights of the lane's element k at y = ln n_e: w_j = exp(lp_j - max lp),
+    // lp_j = sum_{i<j} (ln Phi_i - y)
+    auto weights = [&](int k, double y, double* w) -> double {
         double lp[kMaxStages], mx = 0.0;
         lp[0] = 0.0;
-        for (int j = 1; j < ns[e]; ++j) {
-            lp[j] = lp[j - 1] + lphi[e][j - 1] - y;
+        for (int j = 1; j < ns[k]; ++j) {
+            lp[j] = lp[j - 1] + lphi[k][j - 1] - y;
             mx = fmax(mx, lp[j]);
         }
         double s0 = 0.0;
-        for (int j = 0; j < ns[e]; ++j) {
+        for (int j = 0; j < ns[k]; ++j) {
             w[j] = exp(lp[j] - mx);
             s0 += w[j];
         }
@@ -107,18 +130,21 @@ __global__ void k_populations(int rows, int n_points, int n_el, const double* __
     auto eval = [&](double y, double* g, double* dg) {
         const double ne = exp(y), nn = n_tot - ne;
         double q = 0.0, v = 0.0;
-        for (int e = 0; e < n_el; ++e) {
+        for (int k = 0; k < kPopElPerLane; ++k) {
+            if (ns[k] == 0) continue;
             double w[kMaxStages];
-            const double s0 = weights(e, y, w);
+            const double s0 = weights(k, y, w);
             double s1 = 0.0, s2 = 0.0;
-            for (int j = 1; j < ns[e]; ++j) {
+            for (int j = 1; j < ns[k]; ++j) {
                 s1 += j * w[j];
                 s2 += (double)j * j * w[j];
             }
             const double mean = s1 / s0;
-            q += frac[e] * mean;
-            v += frac[e] * fmax(s2 / s0 - mean * mean, 0.0);
+            q += frac[k] * mean;
+            v += frac[k] * fmax(s2 / s0 - mean * mean, 0.0);
         }
+        q = warp_sum(q);
+        v = warp_sum(v);
         *g = ne - nn * q;
         *dg = ne * (1.0 + q) + nn * v;
     };
@@ -134,22 +160,27 @@ __global__ void k_populations(int rows, int n_points, int n_el, const double* __
         if (fabs(dy) < 1e-14 || !(hi - lo > 0.0) || !(y > lo && y < hi && (0.5 * (lo + hi) != lo))) break;
     }
     const double ne = exp(y), nn = n_tot - ne;
-    double mmean = 0.0, nHI = 0.0;
-    for (int e = 0; e < n_el; ++e) {
+    double mpart = 0.0, nHI = 0.0;
+    for (int k = 0; k < kPopElPerLane; ++k) {
+        const int e = lane + 32 * k;
+        if (e >= n_el) continue;
         double w[kMaxStages];
-        const double s0 = weights(e, y, w);
+        const double s0 = weights(k, y, w);
         for (int j = 0; j < kMaxStages; ++j) {
-            const double nj = j < ns[e] ? frac[e] * nn * w[j] / s0 : 0.0;
-            row[pop_nu(e, j)] = j < ns[e] ? nj / exp(lU[e][j]) : 0.0;
+            const double nj = j < ns[k] ? frac[k] * nn * w[j] / s0 : 0.0;
+            row[pop_nu(e, j)] = j < ns[k] ? nj / exp(lU[k][j]) : 0.0;
             if (e == 0 && j == 0) nHI = nj;
         }
-        mmean += frac[e] * el[e * kElStride + kElMass] * kAMU;
+        mpart += frac[k] * el[e * kElStride + kElMass] * kAMU;
     }
-    row[kPopT] = t;
-    row[kPopP] = p;
-    row[kPopNe] = ne;
-    row[kPopNHI] = nHI;
-    row[kPopRho] = nn * mmean;
+    const double mmean = warp_sum(mpart);
+    if (lane == 0) {
+        row[kPopT] = t;
+        row[kPopP] = p;
+        row[kPopNe] = ne;
+        row[kPopNHI] = nHI;
+        row[kPopRho] = nn * mmean;
+    }
 }
 
 }  // namespace
@@ -157,7 +188,8 @@ __global__ void k_populations(int rows, int n_points, int n_el, const double* __
 int populations_device(int n_el, const double* d_el, const double* d_abund, int n_comp, int n_points,
                        const double* d_T, const double* d_P, double* d_pop, cudaStream_t s) {
     const int rows = n_comp * n_points;
-    k_populations<<<(rows + 63) / 64, 64, 0, s>>>(rows, n_points, n_el, d_el, d_abund, d_T, d_P, d_pop);
+    k_populations<<<(unsigned)(((int64_t)rows * 32 + 127) / 128), 128, 0, s>>>(rows, n_points, n_el, d_el, d_abund,
+                                                                             d_T, d_P, d_pop);
     MPSA_CUDA_TRY(cudaGetLastError());
     return MPSA_OK;
 }

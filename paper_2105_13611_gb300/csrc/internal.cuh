@@ -5,6 +5,11 @@
 
 namespace mpsa {
 
+// Line preparation works on blocks of kPrepLines lines of one row, kPrepThreads threads each
+// (per-block class counts, window-length sums and stable bucket placement) (synth.cu).
+constexpr int kPrepThreads = 256;
+constexpr int kPrepLines = 1024;
+
 // FP64 Saha populations for n_comp x n_points rows (api.cu).
 int populations_device(int n_el, const double* d_el, const double* d_abund, int n_comp, int n_points,
                        const double* d_T, const double* d_P, double* d_pop, cudaStream_t s);

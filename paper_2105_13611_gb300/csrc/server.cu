@@ -101,10 +101,11 @@ namespace mpsa {
 namespace {
 
 size_t synth_scratch_bytes(const mpsa_ctx* c, int rows, int N) {
-    // per (row, line) prep arrays and buckets (~57 B), per-line placement (12 B), tile ranges
-    const size_t nT = (size_t)(N + kTile - 1) / kTile;
-    return (size_t)rows * c->L * 60 + (size_t)c->L * 12 + (size_t)rows * kNumClasses * (nT + 3) * 4 +
-           (size_t)rows * kNumClasses * ((c->L + 255) / 256) * 12 + (1 << 20);
+    // per (row, line) prep arrays, buckets and the crossing-search list (~61 B), per-line
+    // placement (12 B), tile ranges, per (row, prep block) class counts and window-length sums
+    const size_t nT = (size_t)(N + kTile - 1) / kTile, nb = (size_t)(c->L + kPrepLines - 1) / kPrepLines;
+    return (size_t)rows * c->L * 64 + (size_t)c->L * 12 + (size_t)rows * kNumClasses * (nT + 3) * 4 +
+           (size_t)rows * nb * (kNumClasses * 4 + 8) + (1 << 20);
 }
 
 int launch_spectrum(mpsa_server* s, Req* r, Slot& sl) {

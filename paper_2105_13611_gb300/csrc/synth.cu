@@ -106,26 +106,34 @@ __global__ void k_consts(int n_sel, const int* __restrict__ sel, int n_sp, const
 //   Delta nu_D = u / lambda0, a = gamma / (4 pi Delta nu_D),
 //   ln S = ln C_s + ln(gf) - E/kT + ln(1 - e^{-h nu0/kT}) - ln Delta nu_D,
 //   ln kappa0 = ln S + ln H(0, a).
-__global__ void k_kappa0(int64_t L, const int* __restrict__ species, const float* __restrict__ loggf,
+// One thread per line and up to kKappa0Rows rows: the line's data and its three damping
+// constants are read and formed once, then each row's values follow.
+constexpr int kKappa0Rows = 8;
+
+__global__ void k_kappa0(int64_t L, int n_sel, const int* __restrict__ species, const float* __restrict__ loggf,
                          const float* __restrict__ E, const float* __restrict__ lgR, const float* __restrict__ lgS,
                          const float* __restrict__ lgW, const float* __restrict__ lamcm, int n_sp,
                          const RowConst* __restrict__ rc, const SpConst* __restrict__ sc,
                          float* __restrict__ lnS_out, float* __restrict__ a_out, float* __restrict__ lnk0_out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L) return;
-    const RowConst r = rc[s];
-    const SpConst q = sc[(size_t)s * n_sp + species[i]];
-    const float lam = lamcm[i];
-    const float gamma = exp10f(lgR[i]) + exp10f(lgS[i]) * r.ne + exp10f(lgW[i]) * r.nHI;
-    const float a = gamma * lam / (kFourPi * q.u);
-    const float lnDnu = logf(q.u) - logf(lam);
-    const float stim = -expm1f(-r.hc_kT_cm / lam);
-    const float lnS = q.lnC + loggf[i] * kLn10 - E[i] * r.inv_kT_eV + logf(stim) - lnDnu;
-    const size_t o = (size_t)s * L + i;
-    lnS_out[o] = lnS;
-    a_out[o] = a;
-    lnk0_out[o] = lnS + logf(voigt_H(0.f, a));
+    const int sp = species[i];
+    const float lam = lamcm[i], lglam = logf(lam), lg = loggf[i], Ei = E[i];
+    const float gR = exp10f(lgR[i]), gS = exp10f(lgS[i]), gW = exp10f(lgW[i]);
+    const int s1 = min(n_sel, (int)(blockIdx.y + 1) * kKappa0Rows);
+    for (int s = blockIdx.y * kKappa0Rows; s < s1; ++s) {
+        const RowConst r = rc[s];
+        const SpConst q = sc[(size_t)s * n_sp + sp];
+        const float gamma = gR + gS * r.ne + gW * r.nHI;
+        const float a = gamma * lam / (kFourPi * q.u);
+        const float lnDnu = logf(q.u) - lglam;
+        const float stim = -expm1f(-r.hc_kT_cm / lam);
+        const float lnS = q.lnC + lg * kLn10 - Ei * r.inv_kT_eV + logf(stim) - lnDnu;
+        const size_t o = (size_t)s * L + i;
+        lnS_out[o] = lnS;
+        a_out[o] = a;
+        lnk0_out[o] = lnS + logf(voigt_H(0.f, a));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -321,44 +329,112 @@ struct PrepOut {
     unsigned char* cls;
     int* blkcnt;          // [n_sel][kNumClasses][nb]
     long long* wpart;     // [n_sel][nb]
+    int* surv;            // [n_sel][L] lines left for the crossing search, each prep block's together
+    int* nsurv;           // [n_sel] their number
 };
 
-__global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const int* __restrict__ species,
-                                              const int* __restrict__ cpos, const float* __restrict__ fpos,
-                                              int n_sp, const SpConst* __restrict__ sc,
-                                              const float* __restrict__ lnS, const float* __restrict__ av,
-                                              const float* __restrict__ lnk0, const float* __restrict__ ln_tp,
-                                              int nb, PrepOut o) {
-    __shared__ int cnt[kNumClasses];
-    __shared__ long long wsum[8];
-    const int s = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (threadIdx.x < kNumClasses) cnt[threadIdx.x] = 0;
+// k_prep: one CTA of kPrepThreads threads per block of kPrepLines lines of one row.  Every line
+// is tested: its peak against the cut threshold, then the cheap bound below on its window's
+// reach.  The lines that remain are appended, as one run per block, to the row's list for
+// k_windows; the others are marked dropped.  The block's class counts and window-length sum,
+// which k_windows adds to, start at zero here.
+__global__ void __launch_bounds__(kPrepThreads) k_prep(int64_t L, int N, float lnq, const int* __restrict__ species,
+                                                       const int* __restrict__ cpos, const float* __restrict__ fpos,
+                                                       int n_sp, const SpConst* __restrict__ sc,
+                                                       const float* __restrict__ lnS, const float* __restrict__ av,
+                                                       const float* __restrict__ lnk0, const float* __restrict__ ln_tp,
+                                                       int nb, PrepOut o) {
+    __shared__ short s_list[kPrepLines];
+    __shared__ int s_n, s_base;
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int64_t i0 = (int64_t)blockIdx.x * kPrepLines;
+    if (threadIdx.x == 0) s_n = 0;
+    if (threadIdx.x < kNumClasses) o.blkcnt[((size_t)s * kNumClasses + threadIdx.x) * nb + blockIdx.x] = 0;
+    if (threadIdx.x == 0) o.wpart[(size_t)s * nb + blockIdx.x] = 0;
     __syncthreads();
-    long long w = 0;
-    if (i < L) {
-        const size_t q = (size_t)s * L + i;
-        const float ltp = ln_tp[s];
-        unsigned char cls = kDropped;
-        int c = cpos[i];
-        float f = fpos[i];
-        float kv = sc[(size_t)s * n_sp + species[i]].kv;
-        float a = av[q];
-        float srel = 0.f;
-        int jlo = 1, jhi = 0, ilo = 1, ihi = 0;
-        bool reach = lnk0[q] >= ltp;
-        const float rel = fminf(lnS[q] - ltp, 88.f);
-        const float r = expf(-rel);
-        if (reach) {
-            // cheap cull before the crossing search: H(v, a) <= 4a/(sqrt(pi) v^2) + exp(-v^2/4)
-            // (the convolution split at |t| = v/2), so the line stays below the cut beyond vb;
-            // lines whose bound window misses the grid (narrow grids) are dropped here
-            const float vb = fmaxf(sqrtf(8.f * kInvSqrtPi * a / r), 2.f * sqrtf(fmaxf(logf(2.f / r), 0.f))) + 1.f;
-            const float hb = fminf(f + d_red(vb, kv, lnq), 1.0e9f), lb = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f);
-            reach = (double)c + (double)hb + 2.0 >= 0.0 && (double)c + (double)lb - 2.0 <= (double)(N - 1);
+    const float ltp = ln_tp[s];
+    constexpr int kPer = kPrepLines / kPrepThreads;
+    // every load of the thread's lines first, so they are in flight together
+    float lk[kPer], ls[kPer], la[kPer], lf[kPer], lkv[kPer];
+    int lc[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int64_t i = i0 + k * kPrepThreads + threadIdx.x;
+        lk[k] = -INFINITY;
+        if (i < L) {
+            const size_t q = (size_t)s * L + i;
+            lk[k] = lnk0[q];
+            ls[k] = lnS[q];
+            la[k] = av[q];
+            lf[k] = fpos[i];
+            lc[k] = cpos[i];
+            lkv[k] = sc[(size_t)s * n_sp + species[i]].kv;
         }
-        if (reach) {
-            srel = expf(rel);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int off = k * kPrepThreads + threadIdx.x;
+        const int64_t i = i0 + off;
+        bool reach = false;
+        if (i < L) {
+            reach = lk[k] >= ltp;
+            if (reach) {
+                // H(v, a) <= 4a/(sqrt(pi) v^2) + exp(-v^2/4) (the convolution split at |t| = v/2),
+                // so the line stays below the cut beyond vb; lines whose bound window misses the
+                // grid (narrow grids) are dropped here
+                const float r = expf(-fminf(ls[k] - ltp, 88.f));
+                const float a = la[k], kv = lkv[k], f = lf[k];
+                const int c = lc[k];
+                const float vb = fmaxf(sqrtf(8.f * kInvSqrtPi * a / r), 2.f * sqrtf(fmaxf(logf(2.f / r), 0.f))) + 1.f;
+                const float hb = fminf(f + d_red(vb, kv, lnq), 1.0e9f), lb = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f);
+                reach = (double)c + (double)hb + 2.0 >= 0.0 && (double)c + (double)lb - 2.0 <= (double)(N - 1);
+            }
+            // only kept lines are read later (through their bucket), so dropped ones write the class alone
+            if (!reach) o.cls[(size_t)s * L + i] = kDropped;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, reach);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_n, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (reach) s_list[base + __popc(m & ((1u << lane) - 1u))] = (short)off;
+    }
+    __syncthreads();
+    const int n = s_n;
+    if (threadIdx.x == 0 && n > 0) s_base = atomicAdd(&o.nsurv[s], n);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += kPrepThreads) o.surv[(size_t)s * L + s_base + t] = (int)(i0 + s_list[t]);
+}
+
+// k_windows: the outer and inner cut windows of every listed line (crossing searches on the
+// FP32 H), its width class and window length.  Threads run over the row's list, so warps are
+// dense whatever fraction of the lines the cheap bound kept.  The per-block class counts and
+// window-length sums are integer atomics, combined first across the lanes of a warp that
+// hold lines of the same prep block (a block's lines are one run of the list).
+__global__ void __launch_bounds__(kPrepThreads) k_windows(int64_t L, int N, float lnq, const int* __restrict__ species,
+                                                          const int* __restrict__ cpos, const float* __restrict__ fpos,
+                                                          int n_sp, const SpConst* __restrict__ sc,
+                                                          const float* __restrict__ lnS, const float* __restrict__ av,
+                                                          const float* __restrict__ ln_tp, int nb, PrepOut o) {
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int n = o.nsurv[s];
+    const float ltp = ln_tp[s];
+    const int stride = gridDim.x * kPrepThreads;
+    // every lane of a warp runs the same number of passes (the warp-wide combining below)
+    const int t0 = blockIdx.x * kPrepThreads + (threadIdx.x & ~31);
+    for (int tw = t0; tw < n; tw += stride) {
+        const int t = tw + lane;
+        int blk = -1 - lane, key2 = -1;   // lanes past the list: a segment of their own
+        long long w = 0;
+        if (t < n) {
+            const int64_t i = o.surv[(size_t)s * L + t];
+            const size_t q = (size_t)s * L + i;
+            blk = (int)(i / kPrepLines);
+            const float rel = fminf(lnS[q] - ltp, 88.f);
+            const float r = expf(-rel);
+            const int c = cpos[i];
+            const float f = fpos[i], a = av[q], kv = sc[(size_t)s * n_sp + species[i]].kv;
+            unsigned char cl = kDropped;
+            const float srel = expf(rel);
             float vo, vi;
             cut_speeds(a, r, &vo, &vi);
             const float vo2 = vo * (1.f + 1e-5f);
@@ -367,8 +443,8 @@ __global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const
             hi = hi > N - 1 ? N - 1 : hi;
             lo = lo < 0 ? 0 : lo;
             if (lo <= hi) {
-                jlo = (int)lo;
-                jhi = (int)hi;
+                const int jlo = (int)lo, jhi = (int)hi;
+                int ilo = 1, ihi = 0;
                 if (vi >= 0.f) {
                     const float vi2 = vi * (1.f - 1e-5f);
                     long long ih = (long long)c + (long long)floorf(fminf(f + d_red(vi2, kv, lnq), 1.0e9f)) - 2;
@@ -382,35 +458,36 @@ __global__ void __launch_bounds__(256) k_prep(int64_t L, int N, float lnq, const
                 }
                 const int key = c < -1 ? -1 : (c > N ? N : c);
                 const int hw = max(jhi - key, key - jlo);
-                cls = (unsigned char)(32 - __clz(hw));
+                cl = (unsigned char)(32 - __clz(hw));
+                key2 = blk * kNumClasses + cl;
                 w = (long long)(jhi - jlo + 1);
-                atomicAdd(&cnt[cls], 1);
+                o.c[q] = c;
+                o.f[q] = f;
+                o.srel[q] = srel;
+                o.a[q] = a;
+                o.kv[q] = kv;
+                o.jlo[q] = jlo;
+                o.jhi[q] = jhi;
+                o.ilo[q] = ilo;
+                o.ihi[q] = ihi;
             }
+            o.cls[q] = cl;
         }
-        // only kept lines are read later (through their bucket), so dropped ones write the class alone
-        if (cls != kDropped) {
-            o.c[q] = c;
-            o.f[q] = f;
-            o.srel[q] = srel;
-            o.a[q] = a;
-            o.kv[q] = kv;
-            o.jlo[q] = jlo;
-            o.jhi[q] = jhi;
-            o.ilo[q] = ilo;
-            o.ihi[q] = ihi;
+        // window-length sum of each prep block's run of lanes (runs are contiguous): segmented
+        // inclusive scan, the run's last lane adds the total
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, d);
+            const int yb = __shfl_up_sync(0xffffffffu, blk, d);
+            if (lane >= d && yb == blk) w += y;
         }
-        o.cls[q] = cls;
+        const int nextb = __shfl_down_sync(0xffffffffu, blk, 1);
+        if (blk >= 0 && (lane == 31 || nextb != blk) && w > 0)
+            atomicAdd((unsigned long long*)&o.wpart[(size_t)s * nb + blk], (unsigned long long)w);
+        // kept lines per (prep block, class)
+        const unsigned same = __match_any_sync(0xffffffffu, key2);
+        if (key2 >= 0 && lane == __ffs(same) - 1)
+            atomicAdd(&o.blkcnt[((size_t)s * kNumClasses + key2 % kNumClasses) * nb + blk], __popc(same));
     }
-    // block sum of window lengths
-    for (int d = 16; d > 0; d >>= 1) w += __shfl_down_sync(0xffffffffu, w, d);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = w;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long t = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
-        o.wpart[(size_t)s * nb + blockIdx.x] = t;
-    }
-    if (threadIdx.x < kNumClasses) o.blkcnt[((size_t)s * kNumClasses + threadIdx.x) * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
 // k_scan_class: per (class, row), exclusive scan in place of the per-block counts of the
@@ -478,44 +555,59 @@ __global__ void __launch_bounds__(1024) k_scan_fin(int nb, const int* __restrict
     }
 }
 
-// k_scatter: stable placement of kept lines into class buckets (centre order preserved).
-__global__ void __launch_bounds__(256) k_scatter(int64_t L, int N, const unsigned char* __restrict__ cls,
-                                                 const int* __restrict__ cpos, const int* __restrict__ blkoff,
-                                                 const int* __restrict__ classbase, int nb, int* __restrict__ bidx,
-                                                 int* __restrict__ bkey, const PrepOut o, LineRec* __restrict__ rec) {
-    __shared__ int wcnt[8][kNumClasses];
+// k_scatter: stable placement of kept lines into class buckets (centre order preserved), one
+// CTA per prep block of kPrepLines lines, taken kPrepThreads at a time in line order.  A block
+// that kept no line (window-length sum zero) returns at once.
+__global__ void __launch_bounds__(kPrepThreads) k_scatter(int64_t L, int N, const unsigned char* __restrict__ cls,
+                                                          const int* __restrict__ cpos, const int* __restrict__ blkoff,
+                                                          const int* __restrict__ classbase, int nb,
+                                                          int* __restrict__ bidx, int* __restrict__ bkey,
+                                                          const PrepOut o, LineRec* __restrict__ rec) {
+    constexpr int kWarps = kPrepThreads / 32;
+    __shared__ int wcnt[kWarps][kNumClasses];
+    __shared__ int done[kNumClasses];   // lines of each class placed by the earlier passes
     const int s = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o.wpart[(size_t)s * nb + blockIdx.x] == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = threadIdx.x; k < 8 * kNumClasses; k += blockDim.x) (&wcnt[0][0])[k] = 0;
-    __syncthreads();
-    const int b = (i < L) ? (int)cls[(size_t)s * L + i] : (int)kDropped;
-    const unsigned same = __match_any_sync(0xffffffffu, b);
-    const unsigned lt = (1u << lane) - 1u;
-    const int lrank = __popc(same & lt);
-    if (b < kNumClasses && lrank == 0) wcnt[warp][b] = __popc(same);
-    __syncthreads();
-    if (b < kNumClasses) {
-        int before = 0;
-        for (int w = 0; w < warp; ++w) before += wcnt[w][b];
-        const int pos = classbase[s * kNumClasses + b] + blkoff[((size_t)s * kNumClasses + b) * nb + blockIdx.x] +
-                        before + lrank;
-        const int c = cpos[i];
-        bidx[(size_t)s * L + pos] = (int)i;
-        bkey[(size_t)s * L + pos] = c < -1 ? -1 : (c > N ? N : c);
-        const size_t q = (size_t)s * L + i;
-        LineRec r;
-        r.c = o.c[q];
-        r.f = o.f[q];
-        r.kv = o.kv[q];
-        r.a = o.a[q];
-        r.srel = o.srel[q];
-        r.jlo = o.jlo[q];
-        r.jhi = o.jhi[q];
-        r.ilo = o.ilo[q];
-        r.ihi = o.ihi[q];
-        r.pad0 = r.pad1 = r.pad2 = 0;
-        rec[(size_t)s * L + pos] = r;
+    if (threadIdx.x < kNumClasses) done[threadIdx.x] = 0;
+    for (int k = 0; k < kPrepLines / kPrepThreads; ++k) {
+        for (int t = threadIdx.x; t < kWarps * kNumClasses; t += kPrepThreads) (&wcnt[0][0])[t] = 0;
+        __syncthreads();
+        const int64_t i = (int64_t)blockIdx.x * kPrepLines + k * kPrepThreads + threadIdx.x;
+        const int b = (i < L) ? (int)cls[(size_t)s * L + i] : (int)kDropped;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int lrank = __popc(same & ((1u << lane) - 1u));
+        if (b < kNumClasses && lrank == 0) wcnt[warp][b] = __popc(same);
+        __syncthreads();
+        if (b < kNumClasses) {
+            int before = done[b];
+            for (int w = 0; w < warp; ++w) before += wcnt[w][b];
+            const int pos = classbase[s * kNumClasses + b] + blkoff[((size_t)s * kNumClasses + b) * nb + blockIdx.x] +
+                            before + lrank;
+            const int c = cpos[i];
+            bidx[(size_t)s * L + pos] = (int)i;
+            bkey[(size_t)s * L + pos] = c < -1 ? -1 : (c > N ? N : c);
+            const size_t q = (size_t)s * L + i;
+            LineRec r;
+            r.c = o.c[q];
+            r.f = o.f[q];
+            r.kv = o.kv[q];
+            r.a = o.a[q];
+            r.srel = o.srel[q];
+            r.jlo = o.jlo[q];
+            r.jhi = o.jhi[q];
+            r.ilo = o.ilo[q];
+            r.ihi = o.ihi[q];
+            r.pad0 = r.pad1 = r.pad2 = 0;
+            rec[(size_t)s * L + pos] = r;
+        }
+        __syncthreads();
+        if (threadIdx.x < kNumClasses) {
+            int t = 0;
+            for (int w = 0; w < kWarps; ++w) t += wcnt[w][threadIdx.x];
+            done[threadIdx.x] += t;
+        }
+        __syncthreads();
     }
 }
 
@@ -783,6 +875,14 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile, int sp = 0
                                       ((klo == 0 && khi == PTS - 1) ? kFlFull : 0);
                     if (dist >= (float)kFarDist && vmin >= kFarV) {
                         isFar = true;
+                        // a far line whose windows reach the grid's last point counts as covering
+                        // the tile there: the points past the grid's end (last tile only) are
+                        // evaluated but never stored, so narrow grids keep the unmasked forms
+                        const int Te = min(T1, g.N - 1);
+                        const int khf = jhi >= Te ? PTS - 1 : khi;
+                        const bool chf = !(r1.w <= P0 && r2.x >= min(J0 + khf * THREADS + THREADS - 1, Te));
+                        const int ff = klo | (khf << kFlKloBits) | (chf ? kFlChk : 0) |
+                                       ((klo == 0 && khf == PTS - 1) ? kFlFull : 0);
                         const float D = (float)(J0 - c) - f;
                         const float x = D * g.lnq;
                         const float E1 = expm1f(-x), B = expf(-x);
@@ -800,12 +900,12 @@ __device__ __forceinline__ void tile_body(const RowDesc& g, int tile, int sp = 0
                             // every D/sk of the tile within [1e-18, 1e18]: the form in units of sk
                             const bool scaled = sk <= 1.0e18f * (zmin2 - 1.5f) && vmax <= 1.0e9f * sqrtf(sk);
                             fb = make_float4(0.f, 0.f,
-                                             __int_as_float(flags | kFlRat | (yform ? kFlAlt : 0) |
+                                             __int_as_float(ff | kFlRat | (yform ? kFlAlt : 0) |
                                                             (scaled ? kFlScaled : 0)),
                                              0.f);
                         } else {
                             fa = make_float4(r2 * kv * B, r2 * kv * E1, fmaf(2.f, A, -1.f), 8.f * A);
-                            fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(flags | (yform ? kFlAlt : 0)), 0.f);
+                            fb = make_float4(2.f * sk, 4.f * sk, __int_as_float(ff | (yform ? kFlAlt : 0)), 0.f);
                         }
                     } else {
                         isNear = true;
@@ -1204,7 +1304,7 @@ int prep_alloc(PrepBufs& b, const mpsa_ctx* ctx, int n_sel, int N, double R, int
     b.N = N;
     b.tile = tile;
     b.nT = (N + tile - 1) / tile;
-    b.nb = (int)((b.L + 255) / 256);
+    b.nb = (int)((b.L + kPrepLines - 1) / kPrepLines);
     b.lnq = log1p(1.0 / R);
     const int64_t L = b.L;
     const size_t SL = (size_t)n_sel * L;
@@ -1218,7 +1318,7 @@ int prep_alloc(PrepBufs& b, const mpsa_ctx* ctx, int n_sel, int N, double R, int
         (r = al(&b.classbase, (size_t)n_sel * kNumClasses)) || (r = al(&b.classcnt, (size_t)n_sel * kNumClasses)) ||
         (r = al(&b.bidx, SL)) || (r = al(&b.bkey, SL)) || (r = al(&b.rec, SL)) ||
         (r = al(&b.cum, (size_t)n_sel * kNumClasses * (b.nT + 3))) || (r = al(&b.med, n_sel)) ||
-        (r = al(&b.ghist, (size_t)n_sel * kMedBins)))
+        (r = al(&b.ghist, (size_t)n_sel * kMedBins)) || (r = al(&b.po.surv, SL)) || (r = al(&b.po.nsurv, n_sel)))
         return r;
     b.po.blkcnt = b.blkcnt;
     b.po.wpart = b.wpart;
@@ -1240,8 +1340,9 @@ int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const
     const int pop32 = (opts && opts->precision == MPSA_PREC_FP32_POP32) ? 1 : 0;
     k_consts<<<(n_sel * n_sp + 127) / 128, 128, 0, st>>>(n_sel, d_sel, n_sp, ctx->d_sp_el, ctx->d_sp_stage, ctx->n_el,
                                                            ctx->d_el, pop, ctx->vturb, pop32, b.rc, b.spc);
-    k_kappa0<<<dim3(lb, n_sel), 256, 0, st>>>(L, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS,
-                                               ctx->d_lgW, b.lamcm, n_sp, b.rc, b.spc, b.lnS, b.av, b.lnk0);
+    k_kappa0<<<dim3(lb, (n_sel + kKappa0Rows - 1) / kKappa0Rows), 256, 0, st>>>(
+        L, n_sel, ctx->d_species, ctx->d_loggf, ctx->d_E, ctx->d_lgR, ctx->d_lgS, ctx->d_lgW, b.lamcm, n_sp, b.rc,
+        b.spc, b.lnS, b.av, b.lnk0);
     {
         // median of ln kappa0 per row: three radix levels, each a multi-CTA histogram and a pick
         const int per_row = (int)std::max<int64_t>(1, std::min<int64_t>(128, (L + 8191) / 8192));
@@ -1252,12 +1353,23 @@ int prep_launch(const PrepBufs& b, const mpsa_ctx* ctx, const double* pop, const
                                                kc_out);
         }
     }
-    k_prep<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc, b.lnS, b.av,
-                                              b.lnk0, b.ln_tp, b.nb, b.po);
+    MPSA_CUDA_TRY(cudaMemsetAsync(b.po.nsurv, 0, (size_t)n_sel * sizeof(int), st));
+    k_prep<<<dim3(b.nb, n_sel), kPrepThreads, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc,
+                                                       b.lnS, b.av, b.lnk0, b.ln_tp, b.nb, b.po);
+    {
+        // the listed lines' count is known on the device only: about eight CTAs per SM in all,
+        // each running over its row's list
+        int dev = 0, sms = 0;
+        MPSA_CUDA_TRY(cudaGetDevice(&dev));
+        MPSA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int gx = std::max(1, std::min(b.nb, (8 * sms + n_sel - 1) / n_sel));
+        k_windows<<<dim3(gx, n_sel), kPrepThreads, 0, st>>>(L, b.N, (float)b.lnq, ctx->d_species, b.c, b.f, n_sp, b.spc,
+                                                            b.lnS, b.av, b.ln_tp, b.nb, b.po);
+    }
     k_scan_class<<<dim3(kNumClasses, n_sel), 1024, 0, st>>>(b.nb, b.blkcnt, b.classcnt);
     k_scan_fin<<<n_sel, 1024, 0, st>>>(b.nb, b.classcnt, b.classbase, b.wpart, (long long*)evals);
-    k_scatter<<<dim3(b.nb, n_sel), 256, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx, b.bkey,
-                                                 b.po, b.rec);
+    k_scatter<<<dim3(b.nb, n_sel), kPrepThreads, 0, st>>>(L, b.N, b.po.cls, b.c, b.blkcnt, b.classbase, b.nb, b.bidx,
+                                                          b.bkey, b.po, b.rec);
     return ranges_launch(b, b.tile, b.cum, st);
 }
 
