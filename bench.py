@@ -47,9 +47,9 @@ UNIT = "line-evals/s"
 FLOP_PER_EVAL = 6.5
 FP32_LANES_PER_SM = 128
 # kernels of the library per timed step: synth_opacity (k_place, k_consts, k_kappa0, k_med_init,
-# three k_med_hist + k_med_pick levels, k_prep, k_scan_class, k_scan_fin, k_scatter, k_ranges,
-# k_tiles) and build_odf (k_odf_gather, then k_odf for the intervals it leaves)
-LAUNCHES_PER_STEP = 18
+# three k_med_hist + k_med_pick levels, k_prep, k_windows, k_scan_class, k_scan_fin, k_scatter,
+# k_ranges, k_tiles) and build_odf (k_odf_gather, then k_odf for the intervals it leaves)
+LAUNCHES_PER_STEP = 19
 
 
 def parse():

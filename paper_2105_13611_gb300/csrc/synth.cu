@@ -244,20 +244,50 @@ __device__ float v_bound(float a, float t) {
 }
 
 // Crossing of H(v, a) = t by the Illinois variant of regula falsi on ln H against ln v.
-// Invariant: H(e^xlo) >= t > H(e^xhi); the bracket shrinks to a few FP32 ulps of ln v
-// (typically 6-10 evaluations instead of 40 bisection steps).  Returns the verified ends.
+// Invariant: H(e^xlo) >= t > H(e^xhi); the bracket shrinks to a few FP32 ulps of ln v.
+// The search first tries a bracket of +-5 % around ve = max(sqrt(a / (sqrt(pi) t)),
+// sqrt(-ln t)), the crossing of the Lorentz wing a / (sqrt(pi) v^2) or of the Doppler core
+// e^{-v^2}; where H confirms it the search starts there, else from the ends it has verified.
+// Returns the verified ends.
 __device__ void crossing(float a, float t, float vb, float* v_ge, float* v_lt) {
     const float lt = logf(t);
     auto f = [&](float x) {
         const float h = voigt_H(expf(x), a);
         return h > 0.f ? logf(h) - lt : -1.0e4f;
     };
-    float xlo = logf(1e-4f), xhi = logf(vb);
-    float flo = f(xlo), fhi = f(xhi);
-    if (flo < 0.f) {                       // below t already at |v| = 1e-4
-        *v_ge = -1.f;
-        *v_lt = 1e-4f;
-        return;
+    float xlo = logf(1e-4f), xhi = logf(vb), flo, fhi;
+    const float ve = fmaxf(sqrtf(a * kInvSqrtPi / t), sqrtf(fmaxf(-lt, 0.f)));
+    const float xg0 = logf(ve) - 0.05f, xg1 = xg0 + 0.1f;
+    bool probe_lo = true;
+    if (xg0 > xlo && xg1 < xhi) {
+        const float f0 = f(xg0);
+        if (f0 >= 0.f) {                   // H >= t at xg0, so also at |v| = 1e-4
+            probe_lo = false;
+            xlo = xg0;
+            flo = f0;
+            const float f1 = f(xg1);
+            if (f1 < 0.f) {
+                xhi = xg1;
+                fhi = f1;
+            } else {
+                xlo = xg1;
+                flo = f1;
+                fhi = f(xhi);
+            }
+        } else {
+            xhi = xg0;
+            fhi = f0;
+        }
+    } else {
+        fhi = f(xhi);
+    }
+    if (probe_lo) {
+        flo = f(xlo);
+        if (flo < 0.f) {                   // below t already at |v| = 1e-4
+            *v_ge = -1.f;
+            *v_lt = 1e-4f;
+            return;
+        }
     }
     int side = 0;
     // stop at ~2 FP32 ulps of ln v (the ends stay verified, so precision only sets tightness)
@@ -387,7 +417,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(int64_t L, int N, float l
                 const int c = lc[k];
                 const float vb = fmaxf(sqrtf(8.f * kInvSqrtPi * a / r), 2.f * sqrtf(fmaxf(logf(2.f / r), 0.f))) + 1.f;
                 const float hb = fminf(f + d_red(vb, kv, lnq), 1.0e9f), lb = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f);
-                reach = (double)c + (double)hb + 2.0 >= 0.0 && (double)c + (double)lb - 2.0 <= (double)(N - 1);
+                // c + hb + 2 >= 0 and c + lb - 2 <= N - 1 without FP64 (slow on this part): hb >= 0
+                // and lb < 1, so only centres off the grid compare, against integer bounds rounded
+                // towards keeping the line (k_windows drops the few extra ones exactly)
+                reach = (c >= -2 || hb >= __int2float_rd(-2 - c)) && (c <= N || lb <= __int2float_ru(N + 1 - c));
             }
             // only kept lines are read later (through their bucket), so dropped ones write the class alone
             if (!reach) o.cls[(size_t)s * L + i] = kDropped;
@@ -556,34 +589,52 @@ __global__ void __launch_bounds__(1024) k_scan_fin(int nb, const int* __restrict
 }
 
 // k_scatter: stable placement of kept lines into class buckets (centre order preserved), one
-// CTA per prep block of kPrepLines lines, taken kPrepThreads at a time in line order.  A block
-// that kept no line (window-length sum zero) returns at once.
+// CTA per prep block of kPrepLines lines; warp w takes the block's w-th run of consecutive
+// lines.  A first pass counts each warp's lines per class, a scan over the warps gives the
+// offsets, and a second pass places the lines.  A block that kept no line (window-length sum
+// zero) returns at once.
 __global__ void __launch_bounds__(kPrepThreads) k_scatter(int64_t L, int N, const unsigned char* __restrict__ cls,
                                                           const int* __restrict__ cpos, const int* __restrict__ blkoff,
                                                           const int* __restrict__ classbase, int nb,
                                                           int* __restrict__ bidx, int* __restrict__ bkey,
                                                           const PrepOut o, LineRec* __restrict__ rec) {
-    constexpr int kWarps = kPrepThreads / 32;
+    constexpr int kWarps = kPrepThreads / 32, kGroups = kPrepLines / kPrepThreads;
     __shared__ int wcnt[kWarps][kNumClasses];
-    __shared__ int done[kNumClasses];   // lines of each class placed by the earlier passes
     const int s = blockIdx.y;
     if (o.wpart[(size_t)s * nb + blockIdx.x] == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < kNumClasses) done[threadIdx.x] = 0;
-    for (int k = 0; k < kPrepLines / kPrepThreads; ++k) {
-        for (int t = threadIdx.x; t < kWarps * kNumClasses; t += kPrepThreads) (&wcnt[0][0])[t] = 0;
-        __syncthreads();
-        const int64_t i = (int64_t)blockIdx.x * kPrepLines + k * kPrepThreads + threadIdx.x;
-        const int b = (i < L) ? (int)cls[(size_t)s * L + i] : (int)kDropped;
-        const unsigned same = __match_any_sync(0xffffffffu, b);
-        const int lrank = __popc(same & ((1u << lane) - 1u));
-        if (b < kNumClasses && lrank == 0) wcnt[warp][b] = __popc(same);
-        __syncthreads();
-        if (b < kNumClasses) {
-            int before = done[b];
-            for (int w = 0; w < warp; ++w) before += wcnt[w][b];
-            const int pos = classbase[s * kNumClasses + b] + blkoff[((size_t)s * kNumClasses + b) * nb + blockIdx.x] +
-                            before + lrank;
+    for (int t = threadIdx.x; t < kWarps * kNumClasses; t += kPrepThreads) (&wcnt[0][0])[t] = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * kPrepLines + (int64_t)warp * (32 * kGroups) + lane;
+    const unsigned lt = (1u << lane) - 1u;
+    int b[kGroups];
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const int64_t i = i0 + 32 * g;
+        b[g] = (i < L) ? (int)cls[(size_t)s * L + i] : (int)kDropped;
+        const unsigned same = __match_any_sync(0xffffffffu, b[g]);
+        if (b[g] < kNumClasses && __popc(same & lt) == 0) wcnt[warp][b[g]] += __popc(same);
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumClasses) {
+        int run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const int t = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        const int64_t i = i0 + 32 * g;
+        const int bg = b[g];
+        const unsigned same = __match_any_sync(0xffffffffu, bg);
+        const int lrank = __popc(same & lt);
+        if (bg < kNumClasses) {
+            const int pos = classbase[s * kNumClasses + bg] + blkoff[((size_t)s * kNumClasses + bg) * nb + blockIdx.x] +
+                            wcnt[warp][bg] + lrank;
             const int c = cpos[i];
             bidx[(size_t)s * L + pos] = (int)i;
             bkey[(size_t)s * L + pos] = c < -1 ? -1 : (c > N ? N : c);
@@ -601,13 +652,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(int64_t L, int N, cons
             r.pad0 = r.pad1 = r.pad2 = 0;
             rec[(size_t)s * L + pos] = r;
         }
-        __syncthreads();
-        if (threadIdx.x < kNumClasses) {
-            int t = 0;
-            for (int w = 0; w < kWarps; ++w) t += wcnt[w][threadIdx.x];
-            done[threadIdx.x] += t;
-        }
-        __syncthreads();
+        __syncwarp();
+        if (bg < kNumClasses && lrank == 0) wcnt[warp][bg] += __popc(same);
+        __syncwarp();
     }
 }
 
