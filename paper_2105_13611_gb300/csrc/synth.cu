@@ -408,19 +408,21 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(int64_t L, int N, float l
         bool reach = false;
         if (i < L) {
             reach = lk[k] >= ltp;
-            if (reach) {
-                // H(v, a) <= 4a/(sqrt(pi) v^2) + exp(-v^2/4) (the convolution split at |t| = v/2),
-                // so the line stays below the cut beyond vb; lines whose bound window misses the
-                // grid (narrow grids) are dropped here
-                const float r = expf(-fminf(ls[k] - ltp, 88.f));
+            const int c = lc[k];
+            if (reach && (c < -2 || c > N)) {
+                // A centre off the grid: H(v, a) <= 4a/(sqrt(pi) v^2) + exp(-v^2/4) (the convolution
+                // split at |t| = v/2), so the line stays below the cut beyond vb, with
+                // 1/r = s_rel = e^rel, rel = ln S - ln t_p >= 0 (the peak passed).  The line is
+                // kept if its bound window [c + f - d_blue(vb) - 2, c + f + d_red(vb) + 2] reaches
+                // the grid; the grid side's offset is compared in FP32 (FP64 issues slowly on this
+                // part) against an integer bound rounded towards keeping the line (k_windows drops
+                // the few extra ones exactly).  Centres on the grid are kept without a test.
+                const float rel = fminf(ls[k] - ltp, 88.f);
                 const float a = la[k], kv = lkv[k], f = lf[k];
-                const int c = lc[k];
-                const float vb = fmaxf(sqrtf(8.f * kInvSqrtPi * a / r), 2.f * sqrtf(fmaxf(logf(2.f / r), 0.f))) + 1.f;
-                const float hb = fminf(f + d_red(vb, kv, lnq), 1.0e9f), lb = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f);
-                // c + hb + 2 >= 0 and c + lb - 2 <= N - 1 without FP64 (slow on this part): hb >= 0
-                // and lb < 1, so only centres off the grid compare, against integer bounds rounded
-                // towards keeping the line (k_windows drops the few extra ones exactly)
-                reach = (c >= -2 || hb >= __int2float_rd(-2 - c)) && (c <= N || lb <= __int2float_ru(N + 1 - c));
+                const float vb =
+                    fmaxf(sqrtf(8.f * kInvSqrtPi * a * expf(rel)), 2.f * sqrtf(fmaxf(0.69314718f + rel, 0.f))) + 1.f;
+                if (c < -2) reach = fminf(f + d_red(vb, kv, lnq), 1.0e9f) >= __int2float_rd(-2 - c);
+                else reach = fmaxf(f - d_blue(vb, kv, lnq), -1.0e9f) <= __int2float_ru(N + 1 - c);
             }
             // only kept lines are read later (through their bucket), so dropped ones write the class alone
             if (!reach) o.cls[(size_t)s * L + i] = kDropped;
