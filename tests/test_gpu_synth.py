@@ -110,6 +110,35 @@ def test_wide_grid_far_wing_forms():
         assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
 
 
+@pytest.mark.parametrize("lam", [(500.0, 501.0), (500.0, 505.0)])
+def test_narrow_grid_far_lines_cover_the_last_tile(lam):
+    # a window shorter than one 2048-point tile (1 nm at R = 5e5), and one of two tiles whose
+    # second is partial, inside a list spread over 450-560 nm: most lines are far from the
+    # tile, and at these pressures their wings reach the window.  A far line whose windows
+    # reach the grid's last point takes the unmasked forms on the last tile (the points past
+    # the grid's end are evaluated and not stored); dense parity against the oracle
+    w = wl.config_tiny(n_lines=3000, lam=lam, R=5e5, seed=31)
+    w.T = np.array([5000.0, 8000.0, 15000.0, 30000.0])
+    w.P = np.array([1e6, 1e7, 1e8, 1e5])
+    se, ss = wl.species_table(w.n_metals)
+    L = wl.linelist(3000, len(se), 450.0, 560.0, 31)
+    ctx, _ = gpu_context(w, lines=L)
+    kg, kcg, evg = gpu_synth(ctx, w, np.arange(4))
+    lnq = np.log1p(1 / w.grid.R)
+    centre = np.log(L.lam_nm / w.grid.lam0_nm) / lnq
+    far = (centre < -2048) | (centre > kg.shape[1] + 2048)
+    assert far.mean() > 0.9
+    for s in range(4):
+        pl, k, slack, W = oracle_dense(w, L, w.T[s], w.P[s])
+        assert abs(kcg[s] / pl.kappa_c - 1) < 2e-5
+        bad, err, bound = opacity_violations(kg[s], k, pl.kappa_c, slack)
+        assert len(bad) == 0, (s, bad[:5], rel_report(kg[s], k, pl.kappa_c))
+        assert W <= evg[s] <= W + 8 * len(L) + 16
+        lo, hi = sy.windows(pl)
+        # far lines reach the window on every row (the case this test is about)
+        assert np.count_nonzero(far & (hi >= lo)) > 50, s
+
+
 def test_full_size_sampled():
     # the 20,000-line, 575,365-point, 4-point workload in the launch configuration of the benchmark;
     # the oracle evaluates sampled grid points one by one (random points and the cores of strong lines)
