@@ -186,6 +186,28 @@ def test_eos_pure_hydrogen_closed_form():
             assert abs(pop.n_e / pop.n_nuc / x - 1) < 1e-11, (T, P)
 
 
+def test_eos_pure_hydrogen_temperature_dependent_partition_function():
+    # pure hydrogen whose neutral stage has the table's partition function ln U_I = c0 + c1 x + c2 x^2,
+    # x = ln(T / 5040 K), and U_II = 1: the ionised fraction is the pure-hydrogen closed form with
+    # Phi = 2 (U_II / U_I(T)) (2 pi m_e k T / h^2)^{3/2} e^{-chi/kT}, and N/U of stage I is n_HI / U_I(T)
+    c0, c1, c2 = 0.7, 0.3, 0.05
+    lnU = np.zeros((1, 5, 3))
+    lnU[0, 0] = [c0, c1, c2]
+    tab = wl.EosTable(["H"], np.array([1.008]), np.array([12.0]), np.array([2], dtype=np.int32),
+                      np.array([[13.598, 0.0, 0.0, 0.0]]), lnU)
+    k, eV = 1.380649e-16, 1.602176634e-12
+    for T in [3000.0, 5040.0, 9000.0, 20000.0, 50000.0]:
+        x = math.log(T / 5040.0)
+        U1 = math.exp(c0 + c1 * x + c2 * x * x)
+        for P in [1e-2, 1e4, 1e7]:
+            phi = 2 * 1.0 / U1 * (2 * math.pi * 9.1093837015e-28 * k * T / 6.62607015e-27 ** 2) ** 1.5 \
+                * math.exp(-13.598 * eV / (k * T))
+            xi = math.sqrt(phi * k * T / (P + phi * k * T))
+            pop = ph.populations_eos(T, P, tab)
+            assert abs(pop.n_e / pop.n_nuc / xi - 1) < 1e-11, (T, P)
+            assert abs(pop.NU[0, 0] / (pop.n_HI / U1) - 1) < 1e-12, (T, P)
+
+
 def test_eos_helium_three_stages_cubic():
     # pure helium with stages I-III and fixed U: with y = n_e / n_tot, a = Phi_0 / n_tot and
     # b = Phi_1 / n_tot, charge and particle conservation give y^3 + 2a y^2 + (3ab - a) y - 2ab = 0,

@@ -85,6 +85,17 @@ def _windows_one_short(pl, level=1.0):
     return lo, np.where(hi >= lo, hi - 1, hi)
 
 
+def _partition_functions_mutant(dx_sign=1.0, with_c2=True):
+    # U[e, j](T) = exp(c0 + c1 x + c2 x^2) with x's sign or the x^2 term as given
+    def f(eos, T):
+        x = dx_sign * math.log(T / 5040.0)
+        c = np.asarray(eos.lnU, dtype=np.float64)
+        U = np.exp(c[:, :, 0] + c[:, :, 1] * x + (c[:, :, 2] * x * x if with_c2 else 0.0))
+        j = np.arange(c.shape[1])[None, :]
+        return np.where(j < np.asarray(eos.n_stages)[:, None], U, 0.0)
+    return f
+
+
 def _swapped_fraction(axis, x):
     i, f = _cell_weights(axis, x)
     return i, 1.0 - f
@@ -126,6 +137,13 @@ CASES = {
     "Saha equation: 3/2 power dropped": (
         _set(ph, "saha_phi", _saha_no_three_halves),
         [t_ph.test_pure_hydrogen_closed_form]),
+    "partition functions: x^2 term dropped": (
+        _set(ph, "partition_functions", _partition_functions_mutant(with_c2=False)),
+        [t_ph.test_eos_pure_hydrogen_temperature_dependent_partition_function]),
+    "partition functions: x = ln(5040 K / T)": (
+        _set(ph, "partition_functions", _partition_functions_mutant(dx_sign=-1.0)),
+        [t_ph.test_eos_pure_hydrogen_temperature_dependent_partition_function,
+         t_ph.test_eos_partition_function_at_reference_temperature]),
     # ODF step means
     "ODF: widths taken in reverse order": (
         _set(od, "cumulative_widths", lambda widths: _cum_widths(list(widths)[::-1])),
