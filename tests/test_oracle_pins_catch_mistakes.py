@@ -32,10 +32,18 @@ _line_terms = ph.line_terms
 _cum_widths = od.cumulative_widths
 _step_means = od.step_means_sorted
 _planck = spc.planck_lambda
+_formal = spc.formal_solution
 _windows = sy.windows
 _grid_size = sy.grid_size
 _rayleigh = co.rayleigh_hi
 _cell_weights = bi.cell_weights
+
+
+def _bound_without_8(a, r):
+    # the window bound with its Lorentz term sqrt(8a / (sqrt(pi) r)) read as sqrt(a / (sqrt(pi) r))
+    a = np.asarray(a, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    return np.maximum(np.sqrt(a / (math.sqrt(math.pi) * r)), 2.0 * np.sqrt(np.maximum(np.log(2.0 / r), 0.0)))
 
 
 def _terms(change):
@@ -62,6 +70,11 @@ def _formal_constant_source_layers(tau, S, mu):
         I = I * ex + S[d] * (1.0 - ex)
     ex = math.exp(-tau[0] / mu)
     return I * ex + S[0] * (1.0 - ex)
+
+
+def _formal_mu_ignored(tau, S, mu):
+    # the formal solution along the vertical (mu dropped from every optical path)
+    return _formal(tau, S, 1.0)
 
 
 def _optical_depth_left_sum(kappa, m):
@@ -117,6 +130,9 @@ CASES = {
     "voigt: centre shifted by 0.01 Doppler width": (
         _set(t_v, "H", lambda v, a: _H(np.asarray(v, dtype=np.float64) - 0.01, a)),
         [t_v.test_even_and_monotone]),
+    "voigt: window bound without the factor 8 of its Lorentz term": (
+        _set(t_v, "H_upper_bound_v", _bound_without_8),
+        [t_v.test_upper_bound]),
     # line terms and populations
     "line strength: stimulated-emission factor dropped": (
         _set(ph, "line_terms", _terms(lambda t, L, pop: dataclasses.replace(
@@ -151,9 +167,15 @@ CASES = {
     "ODF: values sorted in descending order": (
         _set(od, "step_means_sorted", lambda xs, widths: _step_means(xs[::-1], widths)),
         [t_odf.test_brute_force_rational, t_odf.test_monotone_and_mean]),
+    "ODF: arithmetic means where geometric ones are asked for": (
+        _set(od, "geom_step_means_sorted", lambda xs, widths: _step_means(xs, widths)),
+        [t_odf.test_geometric_brute_force_and_zeros]),
     # spectrum
     "formal solution: linear source term dropped": (
         _set(spc, "formal_solution", _formal_constant_source_layers),
+        [t_sp.test_linear_source_eddington_barbier]),
+    "formal solution: mu dropped from the optical paths": (
+        _set(spc, "formal_solution", _formal_mu_ignored),
         [t_sp.test_linear_source_eddington_barbier]),
     "optical depth: left sum for the trapezoid": (
         _set(spc, "optical_depth", _optical_depth_left_sum),
